@@ -1,0 +1,194 @@
+"""Pins of the oracle's Markov chain against exact laws of the grand canonical
+ensemble (Sec. 2, Eqs. 3-5) and against the cell-list bookkeeping rules of
+Sec. 3.2.5.  None of the expected values comes from the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1408_3764_gb300 import workloads as W
+
+
+def _n_trajectory(trace, n0):
+    step = np.zeros(len(trace), np.int64)
+    acc = trace["accepted"].astype(bool)
+    step[acc & (trace["type"] == 1)] = 1
+    step[acc & (trace["type"] == 2)] = -1
+    return n0 + np.cumsum(step)
+
+
+def _batch_error(x, nb=50):
+    b = np.array_split(x, nb)
+    m = np.array([v.mean() for v in b])
+    return m.std(ddof=1) / math.sqrt(nb)
+
+
+def test_ideal_gas_is_poisson():
+    """eps = 0: P(N) is Poisson(zV), so <N> = Var N = zV, and every displacement
+    is accepted.  The paper's printed sign of mu in Eqs. 4-5 would give
+    <N> = V/z instead; this fixes the textbook reading."""
+    L = 10.0
+    V = L ** 3
+    z = 0.05
+    s = O.System(L, 2.5, [[0.0]], [[1.0]])
+    s.build(W.uniform_positions(20, L, 1), np.zeros(20, np.int32))
+    s.set_energy(s.total_energy())
+    tr, st = s.run_moves(7, 0, 400_000, 1 / 3, 1 / 3, 1 / 3, 0.3, 1.0, [math.log(z)])
+    n = _n_trajectory(tr, 20)[50_000:]
+    assert st.accepted[0] == st.attempted[0]
+    err = _batch_error(n.astype(float))
+    assert abs(n.mean() - z * V) < max(6 * err, 0.5)
+    assert n.var() / (z * V) == pytest.approx(1.0, abs=0.15)
+    assert st.energy == 0.0
+
+
+def test_ideal_gas_mixture_each_species_poisson():
+    """Two ideal species: <N_s> = z_s V independently (per-species insertion and
+    deletion with the per-species acceptance rule)."""
+    L = 10.0
+    V = L ** 3
+    z = [0.03, 0.08]
+    s = O.System(L, 2.5, np.zeros((2, 2)), np.ones((2, 2)))
+    s.build(W.uniform_positions(10, L, 2), (np.arange(10) % 2).astype(np.int32))
+    s.set_energy(0.0)
+    tr, st = s.run_moves(9, 0, 600_000, 0.2, 0.4, 0.4, 0.3, 1.0, [math.log(v) for v in z])
+    acc = tr["accepted"].astype(bool)
+    for sp in range(2):
+        mine = tr["species"] == sp
+        step = np.zeros(len(tr), np.int64)
+        step[acc & mine & (tr["type"] == 1)] = 1
+        step[acc & mine & (tr["type"] == 2)] = -1
+        n = 5 + np.cumsum(step)
+        n = n[100_000:]
+        err = _batch_error(n.astype(float))
+        assert abs(n.mean() - z[sp] * V) < max(6 * err, 0.6)
+        assert n.var() / (z[sp] * V) == pytest.approx(1.0, abs=0.15)
+
+
+def test_dimer_separation_distribution():
+    """Two particles, displacements only: the separation is distributed as
+    r^2 exp(-beta U(r)) for r < L/2 (detailed balance of Eq. 3)."""
+    from scipy.integrate import quad
+
+    L, rc, beta = 6.0, 2.5, 1.0 / 1.2
+    s = O.System(L, rc, [[1.0]], [[1.0]])
+    s.build(np.array([[1.0, 1.0, 1.0], [2.2, 1.0, 1.0]]), np.zeros(2, np.int32))
+    s.set_energy(s.total_energy())
+
+    def u(r):
+        return 4 * (r ** -12 - r ** -6) if r < rc else 0.0
+
+    def w(r):
+        return r * r * math.exp(-beta * u(r))
+
+    edges = np.array([0.9, 1.0, 1.1, 1.25, 1.5, 1.8, 2.1, 2.5, 2.8, 3.0])
+    norm = quad(w, 0.7, 3.0, points=[1.12, 2.5], limit=200)[0]
+    want = np.array([quad(w, a, b, limit=200)[0] / norm for a, b in zip(edges[:-1], edges[1:])])
+    rs = []
+    h = L / 2 ** 32
+    for k in range(150_000):
+        s.run_moves(3, 10 * k, 10, 1.0, 0.0, 0.0, 0.9, beta, [0.0], trace=False)
+        _, X, _, _ = s.state()
+        d = (X[0].astype(np.int64) - X[1].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+        rs.append(math.sqrt(float(((d * h) ** 2).sum())))
+    rs = np.array(rs)
+    rs = rs[rs < 3.0]
+    got = np.histogram(rs, bins=edges)[0] / len(rs)
+    # the mass below 0.9 is ~1e-4; compare bin fractions
+    assert np.allclose(got, want, atol=0.012), (got, want)
+
+
+def test_second_virial_coefficient_low_density():
+    """Low-density interacting gas: <N>/V = z - 2 B2 z^2 + O(z^3) with
+    B2 = -2 pi int_0^rc (exp(-beta U) - 1) r^2 dr for the truncated potential."""
+    from scipy.integrate import quad
+
+    beta, rc = 1.0 / 1.2, 2.5
+    B2 = -2 * math.pi * quad(lambda r: (math.exp(-beta * 4 * (r ** -12 - r ** -6)) - 1) * r * r,
+                             1e-3, rc, points=[1.0, 1.12], limit=400)[0]
+    assert B2 < -1.0  # attractive at T* = 1.2
+    z = 0.005
+    L = (20000.0) ** (1 / 3)
+    V = L ** 3
+    s = O.System(L, rc, [[1.0]], [[1.0]])
+    n0 = 100
+    s.build(W.uniform_positions(n0, L, 4), np.zeros(n0, np.int32))
+    s.set_energy(s.total_energy())
+    tr, st = s.run_moves(5, 0, 1_500_000, 0.2, 0.4, 0.4, 1.0, beta, [math.log(z)])
+    n = _n_trajectory(tr, n0)[200_000:].astype(float)
+    want = (z - 2 * B2 * z * z) * V
+    err = _batch_error(n)
+    assert abs(n.mean() - want) < max(5 * err, 0.8), (n.mean(), want, z * V, err)
+    assert n.mean() - z * V > 0.5 * (want - z * V)
+
+
+def _relaxed(n, L, seed, dmin=0.85):
+    rng = np.random.default_rng(seed)
+    pts = np.zeros((0, 3))
+    while len(pts) < n:
+        p = rng.random(3) * L
+        if len(pts):
+            d = pts - p
+            d -= L * np.rint(d / L)
+            if ((d * d).sum(1) < dmin * dmin).any():
+                continue
+        pts = np.vstack([pts, p])
+    return pts
+
+
+def test_chain_bookkeeping_and_energy_consistency():
+    """After many moves of a two-species system: every particle is listed once,
+    in the cell of its position; the running energy equals the recomputed total
+    energy up to the rounding of the accumulated increments."""
+    L, rc = 11.0, 2.5
+    pos = _relaxed(500, L, 3)
+    types = (np.arange(500) % 3 == 0).astype(np.int32)
+    eps, sigma = W.lorentz_berthelot([1.0, 0.8], [1.0, 1.1])
+    s = O.System(L, rc, eps, sigma)
+    s.build(pos, types)
+    E0 = s.total_energy()
+    s.set_energy(E0)
+    tr, st = s.run_moves(11, 0, 30_000, 0.5, 0.25, 0.25, 0.3, 1 / 1.3, [-2.0, -2.5])
+    cnt, X, cc, refs = s.state()
+    assert cc.sum() == cnt.sum()
+    T = s.T
+    start = np.concatenate([[0], np.cumsum(cc)])
+    seen = set()
+    base = np.concatenate([[0], np.cumsum(cnt)])
+    for c in range(s.ncell):
+        for r in refs[start[c]:start[c + 1]]:
+            sp, i = int(r & 0xFF), int(r >> 8)
+            assert i < cnt[sp]
+            assert (sp, i) not in seen
+            seen.add((sp, i))
+            Pp = X[base[sp] + i].astype(np.uint64)
+            cx = [int((int(v) * T) >> 32) for v in Pp]
+            assert (cx[2] * T + cx[1]) * T + cx[0] == c
+    assert len(seen) == cnt.sum()
+    Ef = s.total_energy()
+    assert st.energy == pytest.approx(Ef, abs=1e-9 * max(1.0, abs(E0)) * 10)
+    assert st.accepted[1] > 0 and st.accepted[2] > 0 and st.accepted[0] > 0
+    # the trace's energy increments add up to the final running energy
+    assert E0 + tr["dU"][tr["accepted"] == 1].sum() == pytest.approx(st.energy, rel=1e-12,
+                                                                      abs=1e-9)
+
+
+def test_chain_is_counter_based_resumable():
+    """Moves [0, a) then [a, b) give the same chain as [0, b) (Philox counters)."""
+    L, rc = 9.0, 2.5
+    pos = _relaxed(200, L, 5)
+    a = O.System(L, rc, [[1.0]], [[1.0]])
+    a.build(pos, np.zeros(200, np.int32))
+    a.set_energy(a.total_energy())
+    b = O.System(L, rc, [[1.0]], [[1.0]])
+    b.build(pos, np.zeros(200, np.int32))
+    b.set_energy(b.total_energy())
+    ta, _ = a.run_moves(3, 0, 5000, 1 / 3, 1 / 3, 1 / 3, 0.3, 0.8, [-2.5])
+    tb1, _ = b.run_moves(3, 0, 2000, 1 / 3, 1 / 3, 1 / 3, 0.3, 0.8, [-2.5])
+    tb2, _ = b.run_moves(3, 2000, 3000, 1 / 3, 1 / 3, 1 / 3, 0.3, 0.8, [-2.5])
+    assert np.array_equal(ta, np.concatenate([tb1, tb2]))
+    sa, sb = a.state(), b.state()
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)

@@ -1,0 +1,226 @@
+/*
+ * gcmc.h -- C ABI of the GB300 grand canonical Monte Carlo (GCMC) hot path
+ * for Lennard-Jones fluids with cell lists, after "An Efficient Cell List
+ * Implementation for Monte Carlo Simulation on GPUs" (Schwiebert et al.,
+ * arXiv 1408.3764).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - One context = one simulation box on one GPU.  All work of a call is
+ *   issued on the CUDA stream given to gcmc_create (NULL = legacy default
+ *   stream); calls that return host results synchronise that stream.
+ * - Pointers marked "device" must point to memory of the context's device;
+ *   "host" pointers to ordinary host memory.  The library never keeps a
+ *   caller pointer beyond the call and never frees caller memory.  All
+ *   internal buffers belong to the context and are freed by gcmc_destroy.
+ * - Errors come back as gcmc_status codes; no C++ exception crosses the ABI.
+ *   gcmc_last_error(ctx) gives a one-line description of the last failure.
+ *   Errors detected on the device (cell overflow, capacity, non-finite
+ *   energy) are read back by the call that launched the work.
+ * - Positions.  The box is cubic with edge L and periodic.  A coordinate x
+ *   is stored on a grid of 2^32 points per edge: X = floor(x * (2^32/L))
+ *   mod 2^32 evaluated in IEEE double exactly in that order; the stored
+ *   position is X * L / 2^32.  Minimum-image separations are exact integer
+ *   differences, the cutoff test r^2 < rc^2 is decided exactly on the
+ *   integer squared grid distance (threshold ceil((rc * 2^32/L)^2), IEEE
+ *   double in that order).
+ * - Cells (Sec. 3.2.2 of the paper): T = floor(L/rc) cells per side, T = 3
+ *   when L < 3 rc; S = L/T.  The cell of grid coordinate X is
+ *   floor(X * T / 2^32); cell id = (cz * T + cy) * T + cx.
+ * - Particles.  Species s owns the dense indices 0 .. N_s-1.  A particle is
+ *   named by the 64-bit id (s << 32) | i.  At gcmc_build_cells the index of a
+ *   particle within its species is its rank among the input particles of
+ *   that species ("species-major order" below lists species 0's particles
+ *   by index, then species 1's, ...).
+ */
+#ifndef GCMC_H
+#define GCMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCMC_MAX_SPECIES 8
+
+typedef enum {
+    GCMC_OK = 0,
+    GCMC_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+    GCMC_ERR_CELL_OVERFLOW = 2, /* a cell would exceed its capacity (Sec. 3.2.2) */
+    GCMC_ERR_CAPACITY = 3,      /* a species would exceed max_particles */
+    GCMC_ERR_NONFINITE = 4,     /* the running energy is not finite */
+    GCMC_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    GCMC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    GCMC_ERR_STATE = 7          /* the call needs cells that were never built */
+} gcmc_status;
+
+typedef enum {
+    GCMC_FP64 = 0, /* pair terms and sums in FP64 */
+    GCMC_FP32 = 1  /* pair terms in FP32, sums and the Metropolis test in FP64 */
+} gcmc_precision;
+
+/* Box, cutoff and force field (Eq. 1 with per-species-pair eps and sigma). */
+typedef struct {
+    double L;              /* box edge, > 0 */
+    double rc;             /* cutoff radius, 0 < rc <= L/2 */
+    int32_t n_species;     /* 1 .. GCMC_MAX_SPECIES */
+    int32_t precision;     /* gcmc_precision */
+    const double *eps;     /* host, n_species x n_species row-major, symmetric, >= 0 */
+    const double *sigma;   /* host, n_species x n_species row-major, symmetric, > 0 */
+    int64_t max_particles; /* per-species index capacity; 0 = 2 * N at first build (>= 1024) */
+    int32_t cell_capacity; /* particles per cell slot array; 0 = automatic (Sec. 3.2.2) */
+    int32_t reserved;      /* must be 0 */
+} gcmc_params;
+
+/* Move mix and thermodynamic state of a GCMC run (Sec. 2, Algorithm 1). */
+typedef struct {
+    double p_disp, p_ins, p_del;       /* move probabilities, >= 0, summing to 1 */
+    double max_disp;                   /* displacement half-width delta, 0 <= delta < L/2 */
+    double beta;                       /* 1 / kT */
+    double log_z[GCMC_MAX_SPECIES];    /* ln z_s = beta mu_s - 3 ln Lambda_s */
+} gcmc_move_mix;
+
+/* Counters of one gcmc_run_moves call (averages over the moves of the call). */
+typedef struct {
+    int64_t attempted[3];  /* displacement, insertion, deletion */
+    int64_t accepted[3];
+    int64_t flagged;       /* trials within tolerance of the acceptance threshold */
+    int64_t moves_done;    /* moves completed (less than asked only on error) */
+    double energy;         /* running total energy after the last move */
+    double sum_energy;     /* sum over the moves of the running energy after the move */
+    double sum_n;          /* sum over the moves of N after the move */
+    int64_t n[GCMC_MAX_SPECIES]; /* particles per species after the last move */
+} gcmc_move_stats;
+
+/* One record per move of gcmc_run_moves (32 bytes). */
+typedef struct {
+    double dU;        /* energy change of the trial (the value added on acceptance) */
+    double lnA;       /* log acceptance ratio; -inf when the move is impossible */
+    double uabs;      /* sum over the evaluated pairs of |4 eps s^12| + |4 eps s^6| */
+    int32_t index;    /* particle index within its species; -1 when none */
+    uint8_t type;     /* 0 displacement, 1 insertion, 2 deletion */
+    uint8_t species;
+    uint8_t accepted;
+    uint8_t flagged;  /* bit 0: near the threshold; bit 1: decided in FP64 */
+} gcmc_trace;
+
+/* Geometry derived from the parameters. */
+typedef struct {
+    int64_t T;             /* cells per side */
+    int64_t n_cells;       /* T^3 */
+    int64_t cell_capacity; /* slot array length per cell */
+    int64_t max_particles; /* per species */
+    uint64_t cutoff_grid2; /* squared-grid-distance cutoff */
+    double h;              /* grid spacing L / 2^32 */
+} gcmc_geometry;
+
+typedef struct gcmc_ctx gcmc_ctx;
+
+/* Creates a context for one box.  Copies the eps/sigma tables (Eq. 1) and
+ * derives the cell grid of Sec. 3.2.2.  stream: a cudaStream_t or NULL.
+ * Allocates nothing on the device until gcmc_build_cells.
+ * Errors: INVALID_ARG (L, rc, species, tables, precision), CUDA. */
+gcmc_status gcmc_create(const gcmc_params *params, void *stream, gcmc_ctx **out);
+
+/* Frees the context and all its device buffers.  NULL is accepted. */
+gcmc_status gcmc_destroy(gcmc_ctx *ctx);
+
+/* Bins n particles into the cell list (Sec. 3.2.1, "Building the Initial
+ * Cell List"): quantises pos, computes each particle's cell, and builds the
+ * cell list with an integer counting sort that keeps input order within a
+ * cell.  pos: device, n x 3 FP64 row-major; species: device, n int32 in
+ * [0, n_species).  Replaces any previous configuration and invalidates the
+ * running energy.  Errors: INVALID_ARG (n < 0, bad species, non-finite
+ * coordinate), CAPACITY, CELL_OVERFLOW (explicit cell_capacity too small),
+ * CUDA. */
+gcmc_status gcmc_build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
+
+/* The compact cell list of the last gcmc_build_cells: cell_start and
+ * cell_count (device, n_cells int32 each) and order (device, n int32: input
+ * indices sorted by cell, input order within a cell).  Any pointer may be
+ * NULL.  Valid only before the first gcmc_run_moves after the build.
+ * Errors: STATE, CUDA. */
+gcmc_status gcmc_cell_list(gcmc_ctx *ctx, int32_t *cell_start, int32_t *cell_count,
+                           int32_t *order);
+
+/* Trial energies (Algorithms 6 and 7; Eq. 1 over the 27 cells around each
+ * point): out[k] = sum over particles j != exclude[k] in the 27 cells of the
+ * cell of pos[k] of U_{species[k], s_j}(r) for r < rc.
+ * pos: device m x 3 FP64 (quantised as above); species: device m int32;
+ * exclude: device m int64 particle ids, -1 = none, or NULL for none;
+ * out: device m FP64; out_abs: device m FP64 (the uabs of gcmc_trace) or NULL.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+gcmc_status gcmc_trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,
+                              const int64_t *exclude, int64_t m, double *out, double *out_abs);
+
+/* Runs moves first_move .. first_move + n_moves - 1 of the Markov chain
+ * (Sec. 2 and Algorithm 1, with the acceptance rules of Eqs. 3-5 read with
+ * the textbook sign of mu) entirely on the device: no host round trip per
+ * move.  Move m draws two Philox4x32-10 blocks with counter
+ * (m mod 2^32, m / 2^32, chain, 0|1) and key (seed mod 2^32, seed / 2^32),
+ * chain = 0 for a single box.  Accepted moves update the cell list in place
+ * (Sec. 3.2.5): swap-with-last removal, append, and a deleted index refilled
+ * by the last index of its species.  The running energy starts from
+ * gcmc_total_energy (computed here when not yet known) and grows by dU.
+ * In FP32 mode a trial within 1e-5 * beta * uabs of the threshold is
+ * re-evaluated in FP64 and decided on that value (trace flag bit 1).
+ * stats: host, may be NULL; trace: device n_moves records, may be NULL.
+ * Errors: STATE, INVALID_ARG (mix), CELL_OVERFLOW, CAPACITY (the chain stops
+ * before the offending move: stats->moves_done tells where), NONFINITE, CUDA. */
+gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
+                           const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+
+/* Full-system cell-list energy E = 1/2 sum_i sum_{j != i in the 27 cells}
+ * U(r_ij), r < rc (Sec. 3.1.1 computes the same sum over all pairs).
+ * Also resets the running energy of the chain to this value.
+ * energy: host.  Errors: STATE, CUDA. */
+gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy);
+
+/* Gradient of the full-system energy (Eq. 1 differentiated):
+ *   dpos[k]   = dE/dr_k (device, N x 3 FP32, species-major order) or NULL;
+ *   deps      = dE/deps[a][b], half of the sum over ordered type pairs (a,b)
+ *               (host, n_species^2 FP64) or NULL;
+ *   dsigma    = dE/dsigma[a][b], same convention, rc fixed (host) or NULL;
+ *   energy    = E (host) or NULL;  virial = sum_{i<j} r U'(r) (host) or NULL.
+ * Errors: STATE, CUDA. */
+gcmc_status gcmc_energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma,
+                             double *energy, double *virial);
+
+/* Particle counts per species (host, n_species int64). */
+gcmc_status gcmc_counts(gcmc_ctx *ctx, int64_t *n_per_species);
+
+/* Copies the current configuration out (all host pointers, any may be NULL):
+ * pos_grid: N x 3 uint32 grid coordinates in species-major order;
+ * cell_count: n_cells int32; cell_refs: N uint32 = (i << 8) | s, the
+ * particles of cell 0 in cell order, then cell 1, ...;
+ * energy: the running energy (NaN when unknown).  Errors: STATE, CUDA. */
+gcmc_status gcmc_get_state(gcmc_ctx *ctx, uint32_t *pos_grid, int32_t *cell_count,
+                           uint32_t *cell_refs, double *energy);
+
+/* Restores a configuration written by gcmc_get_state (host pointers), with
+ * n_per_species (host, n_species int64) and the running energy (NaN =
+ * unknown).  Together with the counter-based moves this resumes a chain bit
+ * for bit.  Errors: INVALID_ARG (inconsistent arrays), CAPACITY,
+ * CELL_OVERFLOW, CUDA. */
+gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const uint32_t *pos_grid,
+                           const int32_t *cell_count, const uint32_t *cell_refs, double energy);
+
+/* Geometry of the context (host out).  Errors: INVALID_ARG. */
+gcmc_status gcmc_get_geometry(gcmc_ctx *ctx, gcmc_geometry *out);
+
+/* Number of CUDA kernels this context has launched so far (host out; a
+ * diagnostic for launch accounting).  Errors: INVALID_ARG. */
+gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out);
+
+/* Last error message of the context (never NULL; "" when none). */
+const char *gcmc_last_error(gcmc_ctx *ctx);
+
+/* Library version string. */
+const char *gcmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCMC_H */

@@ -1,0 +1,44 @@
+/*
+ * gcmc_probe.h -- micro-benchmarks that set the latency floor of one Markov
+ * chain on the GPU (measurement aid; the paper has no counterpart).
+ *
+ * A single chain is a sequence of dependent steps: every move needs the
+ * previous move's outcome.  Its throughput is bounded below by the
+ * dependent latencies one move cannot avoid: two dependent global-memory
+ * round trips served from L2 (the trial particle's record, then its
+ * neighbour cells), one CTA-wide reduction with broadcast, the counter-based
+ * random draw and the logarithm of the Metropolis test.  gcmc_probe_latency
+ * measures each on the current device.
+ */
+#ifndef GCMC_PROBE_H
+#define GCMC_PROBE_H
+
+#include <stdint.h>
+
+#include "gcmc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double l2_hop_ns;      /* one dependent 4-byte load, random over the working set */
+    double sync_round_ns;  /* 256-thread CTA: FP64 warp reductions + 2 barriers + broadcast */
+    double philox_ns;      /* two dependent Philox4x32-10 blocks (one move's words) */
+    double log_ns;         /* one dependent FP64 log */
+    double floor_ns;       /* 2 * l2_hop + sync_round + philox + log */
+    int64_t working_set_bytes;
+} gcmc_probe_result;
+
+/* Runs the probes on the current device and stream (NULL = default stream).
+ * working_set_bytes: size of the pointer-chase buffer (>= 1 MiB, <= 64 MiB;
+ * pick the chain's state size so the loads hit L2 as the chain's do).
+ * Allocates and frees its own buffers.  out: host.
+ * Errors: INVALID_ARG, CUDA. */
+gcmc_status gcmc_probe_latency(void *stream, int64_t working_set_bytes, gcmc_probe_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCMC_PROBE_H */

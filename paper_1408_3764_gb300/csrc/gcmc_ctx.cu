@@ -1,0 +1,421 @@
+// gcmc_ctx.cu -- the C ABI: context lifetime, parameters, geometry, state
+// import/export and error reporting.  Kernels live in gcmc_cells.cu,
+// gcmc_energy.cu and gcmc_chain.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gcmc_ctx.h"
+
+namespace gcmc {
+
+gcmc_status fail(gcmc_ctx *ctx, gcmc_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+gcmc_status cuda_fail(gcmc_ctx *ctx, cudaError_t e, const char *where)
+{
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %d (%s) at %s", (int)e, cudaGetErrorString(e), where);
+    if (ctx) ctx->err = buf;
+    return GCMC_ERR_CUDA;
+}
+
+gcmc_status ensure_scratch(gcmc_ctx *ctx, size_t bytes)
+{
+    if (ctx->scratch_bytes >= bytes) return GCMC_OK;
+    if (ctx->scratch) GCMC_CUDA(ctx, cudaFree(ctx->scratch));
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    GCMC_CUDA(ctx, cudaMalloc(&ctx->scratch, bytes));
+    ctx->scratch_bytes = bytes;
+    return GCMC_OK;
+}
+
+gcmc_status ensure_red(gcmc_ctx *ctx, size_t n)
+{
+    if (ctx->d_red_len >= n) return GCMC_OK;
+    if (ctx->d_red) GCMC_CUDA(ctx, cudaFree(ctx->d_red));
+    ctx->d_red = nullptr;
+    ctx->d_red_len = 0;
+    GCMC_CUDA(ctx, cudaMalloc(&ctx->d_red, n * sizeof(double)));
+    ctx->d_red_len = n;
+    return GCMC_OK;
+}
+
+gcmc_status ensure_pinned(gcmc_ctx *ctx, size_t bytes)
+{
+    if (ctx->h_pinned_bytes >= bytes) return GCMC_OK;
+    if (ctx->h_pinned) GCMC_CUDA(ctx, cudaFreeHost(ctx->h_pinned));
+    ctx->h_pinned = nullptr;
+    ctx->h_pinned_bytes = 0;
+    GCMC_CUDA(ctx, cudaMallocHost(&ctx->h_pinned, bytes));
+    ctx->h_pinned_bytes = bytes;
+    return GCMC_OK;
+}
+
+gcmc_status read_status(gcmc_ctx *ctx, int *bits)
+{
+    GCMC_CUDA(ctx, cudaMemcpyAsync(bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GCMC_OK;
+}
+
+static void free_device(gcmc_ctx *ctx)
+{
+    void *ptrs[] = {ctx->cell_pos, ctx->cell_count, ctx->pos_by_id, ctx->d_n, ctx->d_status,
+                    ctx->d_energy, ctx->cell_start, ctx->cpos, ctx->order, ctx->scratch, ctx->d_red};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->cell_pos = nullptr;
+    ctx->cell_count = nullptr;
+    ctx->pos_by_id = nullptr;
+    ctx->d_n = nullptr;
+    ctx->d_status = nullptr;
+    ctx->d_energy = nullptr;
+    ctx->cell_start = nullptr;
+    ctx->cpos = nullptr;
+    ctx->order = nullptr;
+    ctx->scratch = nullptr;
+    ctx->d_red = nullptr;
+    ctx->h_pinned = nullptr;
+    ctx->scratch_bytes = ctx->d_red_len = ctx->h_pinned_bytes = 0;
+}
+
+}  // namespace gcmc
+
+using namespace gcmc;
+
+extern "C" {
+
+gcmc_status gcmc_create(const gcmc_params *p, void *stream, gcmc_ctx **out)
+{
+    if (!out) return GCMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p || !p->eps || !p->sigma) return GCMC_ERR_INVALID_ARG;
+    if (!(p->L > 0.0) || !std::isfinite(p->L) || !(p->rc > 0.0) || 2.0 * p->rc > p->L)
+        return GCMC_ERR_INVALID_ARG;
+    if (p->n_species < 1 || p->n_species > kMaxSpecies) return GCMC_ERR_INVALID_ARG;
+    if (p->precision != GCMC_FP64 && p->precision != GCMC_FP32) return GCMC_ERR_INVALID_ARG;
+    if (p->max_particles < 0 || p->max_particles > (1ll << 24)) return GCMC_ERR_INVALID_ARG;
+    if (p->cell_capacity < 0 || p->cell_capacity > 65535 || p->reserved != 0)
+        return GCMC_ERR_INVALID_ARG;
+    const int S = p->n_species;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            double e = p->eps[a * S + b], s = p->sigma[a * S + b];
+            if (!(e >= 0.0) || !std::isfinite(e) || !(s > 0.0) || !std::isfinite(s))
+                return GCMC_ERR_INVALID_ARG;
+            if (e != p->eps[b * S + a] || s != p->sigma[b * S + a]) return GCMC_ERR_INVALID_ARG;
+        }
+    gcmc_ctx *ctx = new gcmc_ctx();
+    ctx->L = p->L;
+    ctx->rc = p->rc;
+    ctx->q = 4294967296.0 / p->L;
+    ctx->h = p->L / 4294967296.0;
+    ctx->V = p->L * p->L * p->L;
+    ctx->S = S;
+    ctx->precision = p->precision;
+    // cells per side (Sec. 3.2.2): largest T with L/T >= rc, at least 3
+    double t = std::floor(p->L / p->rc);
+    ctx->T = t < 3.0 ? 3 : (int)t;
+    if ((double)ctx->T * ctx->T * ctx->T > 2.0e9) {
+        delete ctx;
+        return GCMC_ERR_INVALID_ARG;
+    }
+    ctx->ncell = (int64_t)ctx->T * ctx->T * ctx->T;
+    {
+        const double rq = p->rc * ctx->q;
+        ctx->R2 = (uint64_t)std::ceil(rq * rq);
+    }
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            const double e = p->eps[a * S + b], s = p->sigma[a * S + b];
+            ctx->eps[a * kMaxSpecies + b] = e;
+            ctx->sigma[a * kMaxSpecies + b] = s;
+            const double sg = s * ctx->q;
+            ctx->fd.c4e[a * kMaxSpecies + b] = 4.0 * e;
+            ctx->fd.sig2[a * kMaxSpecies + b] = sg * sg;
+            ctx->ff.c4e[a * kMaxSpecies + b] = (float)(4.0 * e);
+            ctx->ff.sig2[a * kMaxSpecies + b] = (float)(sg * sg);
+        }
+    ctx->max_particles_req = p->max_particles;
+    ctx->cap_req = p->cell_capacity;
+    ctx->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    int optin = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    ctx->smem_optin = (size_t)optin;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_energy, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_n, sizeof(int64_t) * kMaxSpecies);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_n, 0, sizeof(int64_t) * kMaxSpecies);
+    if (e != cudaSuccess) {
+        free_device(ctx);
+        delete ctx;
+        return GCMC_ERR_CUDA;
+    }
+    *out = ctx;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_destroy(gcmc_ctx *ctx)
+{
+    if (!ctx) return GCMC_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_device(ctx);
+    delete ctx;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (n < 0 || n > (int64_t)kMaxSpecies * (1ll << 24) || (n > 0 && (!pos || !species)))
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_build_cells: bad n or NULL arrays");
+    return build_cells(ctx, pos, species, n);
+}
+
+gcmc_status gcmc_cell_list(gcmc_ctx *ctx, int32_t *cell_start, int32_t *cell_count, int32_t *order)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built || !ctx->order_valid)
+        return fail(ctx, GCMC_ERR_STATE, "gcmc_cell_list: no fresh build");
+    gcmc_status st = make_compact(ctx);
+    if (st != GCMC_OK) return st;
+    if (cell_start)
+        GCMC_CUDA(ctx, cudaMemcpyAsync(cell_start, ctx->cell_start, ctx->ncell * sizeof(int32_t),
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+    if (cell_count)
+        GCMC_CUDA(ctx, cudaMemcpyAsync(cell_count, ctx->cell_count, ctx->ncell * sizeof(int32_t),
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+    if (order && ctx->n_build > 0)
+        GCMC_CUDA(ctx, cudaMemcpyAsync(order, ctx->order, ctx->n_build * sizeof(int32_t),
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,
+                              const int64_t *exclude, int64_t m, double *out, double *out_abs)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_trial_energy: cells not built");
+    if (m < 0 || (m > 0 && (!pos || !species || !out)) || m > (1ll << 31))
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_trial_energy: bad m or NULL arrays");
+    if (m == 0) return GCMC_OK;
+    return trial_energy(ctx, pos, species, exclude, m, out, out_abs);
+}
+
+gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
+                           const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves: cells not built");
+    if (!mix || n_moves < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: bad args");
+    const double ps = mix->p_disp + mix->p_ins + mix->p_del;
+    if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
+        !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L) || !(mix->beta >= 0.0) ||
+        !std::isfinite(mix->beta))
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: bad move mix");
+    for (int s = 0; s < ctx->S; ++s)
+        if (!std::isfinite(mix->log_z[s]))
+            return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: log_z not finite");
+    return run_moves(ctx, seed, first_move, n_moves, mix, stats, trace);
+}
+
+gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_total_energy: cells not built");
+    return total_energy(ctx, energy);
+}
+
+gcmc_status gcmc_energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma,
+                             double *energy, double *virial)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_energy_grad: cells not built");
+    return energy_grad(ctx, dpos, deps, dsigma, energy, virial);
+}
+
+gcmc_status gcmc_counts(gcmc_ctx *ctx, int64_t *n)
+{
+    if (!ctx || !n) return GCMC_ERR_INVALID_ARG;
+    for (int s = 0; s < ctx->S; ++s) n[s] = ctx->built ? ctx->n_host[s] : 0;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_get_state(gcmc_ctx *ctx, uint32_t *pos_grid, int32_t *cell_count,
+                           uint32_t *cell_refs, double *energy)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_get_state: cells not built");
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (pos_grid) {
+        std::vector<uint4> buf;
+        int64_t row = 0;
+        for (int s = 0; s < ctx->S; ++s) {
+            const int64_t ns = ctx->n_host[s];
+            buf.resize((size_t)ns);
+            if (ns > 0)
+                GCMC_CUDA(ctx, cudaMemcpy(buf.data(), ctx->pos_by_id + (size_t)s * ctx->maxN,
+                                          ns * sizeof(uint4), cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < ns; ++i, ++row) {
+                pos_grid[3 * row + 0] = buf[i].x;
+                pos_grid[3 * row + 1] = buf[i].y;
+                pos_grid[3 * row + 2] = buf[i].z;
+            }
+        }
+    }
+    if (cell_count || cell_refs) {
+        std::vector<int32_t> cc((size_t)ctx->ncell);
+        GCMC_CUDA(ctx, cudaMemcpy(cc.data(), ctx->cell_count, ctx->ncell * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost));
+        if (cell_count) memcpy(cell_count, cc.data(), ctx->ncell * sizeof(int32_t));
+        if (cell_refs) {
+            std::vector<uint4> cp((size_t)ctx->ncell * ctx->cap);
+            GCMC_CUDA(ctx, cudaMemcpy(cp.data(), ctx->cell_pos, cp.size() * sizeof(uint4),
+                                      cudaMemcpyDeviceToHost));
+            int64_t k = 0;
+            for (int64_t c = 0; c < ctx->ncell; ++c)
+                for (int j = 0; j < cc[c]; ++j) cell_refs[k++] = cp[(size_t)c * ctx->cap + j].w;
+        }
+    }
+    if (energy) *energy = ctx->energy_valid ? ctx->energy : NAN;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const uint32_t *pos_grid,
+                           const int32_t *cell_count, const uint32_t *cell_refs, double energy)
+{
+    if (!ctx || !n_per_species) return GCMC_ERR_INVALID_ARG;
+    const int S = ctx->S;
+    int64_t N = 0, base[kMaxSpecies + 1] = {0};
+    int64_t nmax = 0;
+    for (int s = 0; s < S; ++s) {
+        if (n_per_species[s] < 0 || n_per_species[s] > (1ll << 24))
+            return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: bad counts");
+        base[s] = N;
+        N += n_per_species[s];
+        if (n_per_species[s] > nmax) nmax = n_per_species[s];
+    }
+    if (N > 0 && (!pos_grid || !cell_count || !cell_refs))
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: NULL arrays");
+    // validate the cell list against the positions
+    int64_t tot = 0, maxc = 0;
+    for (int64_t c = 0; c < ctx->ncell; ++c) {
+        if (cell_count[c] < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: count < 0");
+        tot += cell_count[c];
+        if (cell_count[c] > maxc) maxc = cell_count[c];
+    }
+    if (tot != N) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: counts do not sum to N");
+    std::vector<char> seen((size_t)N, 0);
+    {
+        int64_t k = 0;
+        const uint32_t T = (uint32_t)ctx->T;
+        for (int64_t c = 0; c < ctx->ncell; ++c)
+            for (int j = 0; j < cell_count[c]; ++j, ++k) {
+                const uint32_t r = cell_refs[k];
+                const int s = (int)(r & 0xFF);
+                const int64_t i = r >> 8;
+                if (s >= S || i >= n_per_species[s])
+                    return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: bad reference");
+                const int64_t row = base[s] + i;
+                if (seen[row]) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: duplicate");
+                seen[row] = 1;
+                const uint32_t *P = pos_grid + 3 * row;
+                const int64_t cx = (int64_t)(((uint64_t)P[0] * T) >> 32);
+                const int64_t cy = (int64_t)(((uint64_t)P[1] * T) >> 32);
+                const int64_t cz = (int64_t)(((uint64_t)P[2] * T) >> 32);
+                if ((cz * T + cy) * T + cx != c)
+                    return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: particle in wrong cell");
+            }
+    }
+    // (re)allocate to fit
+    int64_t want_maxN = ctx->max_particles_req > 0 ? ctx->max_particles_req
+                                                    : std::max<int64_t>(1024, 2 * nmax);
+    if (nmax > want_maxN) return fail(ctx, GCMC_ERR_CAPACITY, "gcmc_set_state: above max_particles");
+    int want_cap = ctx->cap_req > 0 ? ctx->cap_req : (int)(((maxc * 5 / 4 + 8) + 7) / 8 * 8);
+    if (want_cap < 8) want_cap = 8;
+    if (maxc > want_cap) return fail(ctx, GCMC_ERR_CELL_OVERFLOW, "gcmc_set_state: cell too full");
+    if (ctx->cell_pos) cudaFree(ctx->cell_pos);
+    if (ctx->cell_count) cudaFree(ctx->cell_count);
+    if (ctx->pos_by_id) cudaFree(ctx->pos_by_id);
+    ctx->cell_pos = nullptr;
+    ctx->cell_count = nullptr;
+    ctx->pos_by_id = nullptr;
+    ctx->maxN = want_maxN;
+    ctx->cap = want_cap;
+    GCMC_CUDA(ctx, cudaMalloc(&ctx->cell_pos, (size_t)ctx->ncell * ctx->cap * sizeof(uint4)));
+    GCMC_CUDA(ctx, cudaMalloc(&ctx->cell_count, (size_t)ctx->ncell * sizeof(int32_t)));
+    GCMC_CUDA(ctx, cudaMalloc(&ctx->pos_by_id, (size_t)S * ctx->maxN * sizeof(uint4)));
+    std::vector<uint4> cp((size_t)ctx->ncell * ctx->cap, make_uint4(0, 0, 0, 0));
+    std::vector<uint4> pb((size_t)S * ctx->maxN, make_uint4(0, 0, 0, 0));
+    int64_t k = 0;
+    for (int64_t c = 0; c < ctx->ncell; ++c)
+        for (int j = 0; j < cell_count[c]; ++j, ++k) {
+            const uint32_t r = cell_refs[k];
+            const int s = (int)(r & 0xFF);
+            const int64_t row = base[s] + (r >> 8);
+            const uint4 v = make_uint4(pos_grid[3 * row], pos_grid[3 * row + 1], pos_grid[3 * row + 2], r);
+            cp[(size_t)c * ctx->cap + j] = v;
+            pb[(size_t)s * ctx->maxN + (r >> 8)] = v;
+        }
+    GCMC_CUDA(ctx, cudaMemcpy(ctx->cell_pos, cp.data(), cp.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    GCMC_CUDA(ctx, cudaMemcpy(ctx->cell_count, cell_count, ctx->ncell * sizeof(int32_t),
+                              cudaMemcpyHostToDevice));
+    GCMC_CUDA(ctx, cudaMemcpy(ctx->pos_by_id, pb.data(), pb.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    int64_t nn[kMaxSpecies] = {0};
+    for (int s = 0; s < S; ++s) nn[s] = n_per_species[s];
+    GCMC_CUDA(ctx, cudaMemcpy(ctx->d_n, nn, sizeof(nn), cudaMemcpyHostToDevice));
+    for (int s = 0; s < kMaxSpecies; ++s) ctx->n_host[s] = nn[s];
+    GCMC_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    ctx->built = true;
+    ctx->compact_valid = false;
+    ctx->order_valid = false;
+    ctx->n_build = N;
+    ctx->energy = energy;
+    ctx->energy_valid = !std::isnan(energy);
+    if (ctx->energy_valid)
+        GCMC_CUDA(ctx, cudaMemcpy(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_get_geometry(gcmc_ctx *ctx, gcmc_geometry *out)
+{
+    if (!ctx || !out) return GCMC_ERR_INVALID_ARG;
+    out->T = ctx->T;
+    out->n_cells = ctx->ncell;
+    out->cell_capacity = ctx->cap;
+    out->max_particles = ctx->maxN;
+    out->cutoff_grid2 = ctx->R2;
+    out->h = ctx->h;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out)
+{
+    if (!ctx || !out) return GCMC_ERR_INVALID_ARG;
+    *out = ctx->launches;
+    return GCMC_OK;
+}
+
+const char *gcmc_last_error(gcmc_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+const char *gcmc_version(void) { return "gcmc-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// gcmc_ctx.h -- the context object behind the C ABI and the launchers each
+// kernel file provides.  Host-side only (no device code).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gcmc.h"
+#include "gcmc_device.cuh"
+
+struct gcmc_ctx {
+    // ---- parameters and derived geometry
+    double L = 0, rc = 0, h = 0, q = 0, V = 0;
+    int S = 1;
+    int precision = GCMC_FP64;
+    double eps[gcmc::kMaxSpecies * gcmc::kMaxSpecies] = {};
+    double sigma[gcmc::kMaxSpecies * gcmc::kMaxSpecies] = {};
+    int T = 3;
+    int64_t ncell = 27;
+    uint64_t R2 = 0;
+    int64_t max_particles_req = 0;  // 0 = automatic
+    int cap_req = 0;                // 0 = automatic
+    int64_t maxN = 0;               // per species, as allocated
+    int cap = 0;                    // per cell, as allocated
+    gcmc::FieldF ff{};
+    gcmc::FieldD fd{};
+
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+
+    // ---- configuration on the device
+    bool built = false;
+    int64_t n_host[gcmc::kMaxSpecies] = {};  // mirror of d_n after each call
+    int64_t n_build = 0;                     // particles at the last build
+    uint4 *cell_pos = nullptr;    // ncell * cap: (X, Y, Z, tag), padded cell-major
+    int32_t *cell_count = nullptr;  // ncell
+    uint4 *pos_by_id = nullptr;   // S * maxN
+    int64_t *d_n = nullptr;       // S counts
+    int32_t *d_status = nullptr;  // device status bits
+    double *d_energy = nullptr;   // running energy (1 double)
+    // compact layout (valid when compact_valid)
+    bool compact_valid = false;
+    int32_t *cell_start = nullptr;  // ncell + 1
+    uint4 *cpos = nullptr;          // maxN_total, compact cell-major
+    int64_t cpos_len = 0;
+    int32_t *order = nullptr;       // n_build (input indices sorted by cell)
+    bool order_valid = false;
+    // scratch
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *d_red = nullptr;        // reduction partials
+    size_t d_red_len = 0;
+    void *h_pinned = nullptr;       // small pinned host staging
+    size_t h_pinned_bytes = 0;
+
+    double energy = 0.0;
+    bool energy_valid = false;
+    int64_t launches = 0;  // kernels this context has launched
+
+    std::string err;
+};
+
+namespace gcmc {
+
+gcmc_status fail(gcmc_ctx *ctx, gcmc_status st, const std::string &msg);
+gcmc_status cuda_fail(gcmc_ctx *ctx, cudaError_t e, const char *where);
+#define GCMC_CUDA(ctx, call)                                        \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return gcmc::cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+gcmc_status ensure_scratch(gcmc_ctx *ctx, size_t bytes);
+gcmc_status ensure_red(gcmc_ctx *ctx, size_t n);
+gcmc_status ensure_pinned(gcmc_ctx *ctx, size_t bytes);
+gcmc_status read_status(gcmc_ctx *ctx, int *bits);
+
+// cells.cu
+gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
+gcmc_status make_compact(gcmc_ctx *ctx);
+gcmc_status relayout(gcmc_ctx *ctx, int new_cap, int64_t new_maxN);
+
+// energy.cu
+gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,
+                         const int64_t *exclude, int64_t m, double *out, double *out_abs);
+gcmc_status total_energy(gcmc_ctx *ctx, double *energy);
+gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
+                        double *virial);
+
+// chain.cu
+gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves,
+                      const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+
+}  // namespace gcmc

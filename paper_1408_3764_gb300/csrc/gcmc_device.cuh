@@ -1,0 +1,192 @@
+// gcmc_device.cuh -- device-side building blocks of the GCMC hot path:
+// counter-based random numbers, grid/cell arithmetic and the Lennard-Jones
+// pair term (Eq. 1) in FP32 and FP64.  Included by every kernel file.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gcmc {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32->64-bit
+// multiplies whose halves are mixed with the other counter words and the
+// key; the key advances by the two Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct Words8 {
+    uint32_t w[8];
+};
+
+__device__ __forceinline__ uint4 philox_block(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a0 = 0xD2511F53u * c.x;  // low half of M0 * c0
+        const uint32_t h0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t a1 = 0xCD9E8D57u * c.z;  // low half of M1 * c2
+        const uint32_t h1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(h1 ^ c.y ^ k.x, a1, h0 ^ c.w ^ k.y, a0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The eight words of move m of chain `chain`.
+__device__ __forceinline__ Words8 move_words(uint64_t seed, uint64_t m, uint32_t chain)
+{
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint4 a = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), chain, 0u), key);
+    const uint4 b = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), chain, 1u), key);
+    Words8 r;
+    r.w[0] = a.x; r.w[1] = a.y; r.w[2] = a.z; r.w[3] = a.w;
+    r.w[4] = b.x; r.w[5] = b.y; r.w[6] = b.z; r.w[7] = b.w;
+    return r;
+}
+
+// 53-bit uniform in [0, 1) from words 6 and 7.
+__device__ __forceinline__ double uniform53(uint32_t w6, uint32_t w7)
+{
+    const uint64_t k = ((uint64_t)(w6 >> 5) << 26) | (uint64_t)(w7 >> 6);
+    return (double)k * 1.1102230246251565404e-16;  // 2^-53
+}
+
+// ---------------------------------------------------------------------------
+// Grid and cells
+// ---------------------------------------------------------------------------
+// floor(X * T / 2^32): the cell coordinate of grid coordinate X.
+__device__ __forceinline__ int cell_coord(uint32_t X, uint32_t T) { return (int)__umulhi(X, T); }
+
+__device__ __forceinline__ int cell_of(uint32_t X, uint32_t Y, uint32_t Z, int T)
+{
+    return (cell_coord(Z, (uint32_t)T) * T + cell_coord(Y, (uint32_t)T)) * T +
+           cell_coord(X, (uint32_t)T);
+}
+
+// Cell id of the neighbour at offset (ox, oy, oz) in {-1,0,1}^3.
+__device__ __forceinline__ int neighbour_cell(int cx, int cy, int cz, int k, int T)
+{
+    int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
+    int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+    nx += (nx < 0) ? T : 0;
+    nx -= (nx >= T) ? T : 0;
+    ny += (ny < 0) ? T : 0;
+    ny -= (ny >= T) ? T : 0;
+    nz += (nz < 0) ? T : 0;
+    nz -= (nz >= T) ? T : 0;
+    return (nz * T + ny) * T + nx;
+}
+
+// Particle tag stored in the 4th word of a position: (index << 8) | species.
+__device__ __forceinline__ uint32_t make_tag(uint32_t i, uint32_t s) { return (i << 8) | s; }
+__device__ __forceinline__ uint32_t tag_species(uint32_t t) { return t & 0xFFu; }
+__device__ __forceinline__ uint32_t tag_index(uint32_t t) { return t >> 8; }
+
+// Exact squared grid distance of the minimum image (the uint32 difference
+// reinterpreted as int32 is the periodic image nearest to zero).
+struct GridSep {
+    int dx, dy, dz;
+    unsigned long long g;
+};
+
+__device__ __forceinline__ GridSep grid_sep(uint4 a, uint4 b)
+{
+    GridSep s;
+    s.dx = (int)(a.x - b.x);
+    s.dy = (int)(a.y - b.y);
+    s.dz = (int)(a.z - b.z);
+    s.g = (unsigned long long)((long long)s.dx * s.dx) + (unsigned long long)((long long)s.dy * s.dy) +
+          (unsigned long long)((long long)s.dz * s.dz);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Force-field constants, per species pair, in grid units:
+//   c4e = 4 eps,  sig2 = (sigma / h)^2,
+//   U = c4e (s^6 s^6 - s^6) with s^2 = sig2 / r_grid^2.
+// ---------------------------------------------------------------------------
+struct FieldF {
+    float c4e[kMaxSpecies * kMaxSpecies];
+    float sig2[kMaxSpecies * kMaxSpecies];
+};
+struct FieldD {
+    double c4e[kMaxSpecies * kMaxSpecies];
+    double sig2[kMaxSpecies * kMaxSpecies];
+};
+
+// Pair energy in FP32 from an exact grid separation known to be inside the
+// cutoff.  rep/att are the two terms' magnitudes.
+__device__ __forceinline__ void lj_f32(const GridSep &s, float c4e, float sig2, float &u, float &mag)
+{
+    const float fx = (float)s.dx, fy = (float)s.dy, fz = (float)s.dz;
+    const float r2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    const float s2 = sig2 / r2;
+    const float s6 = s2 * s2 * s2;
+    const float rep = c4e * s6 * s6;
+    const float att = c4e * s6;
+    u = rep - att;
+    mag = rep + att;
+    if (s.g == 0ull) {
+        u = __int_as_float(0x7f800000);
+        mag = u;
+    }
+}
+
+__device__ __forceinline__ void lj_f64(const GridSep &s, double c4e, double sig2, double &u,
+                                       double &mag)
+{
+    const double fx = (double)s.dx, fy = (double)s.dy, fz = (double)s.dz;
+    const double r2 = fx * fx + fy * fy + fz * fz;
+    const double s2 = sig2 / r2;
+    const double s6 = s2 * s2 * s2;
+    const double rep = c4e * s6 * s6;
+    const double att = c4e * s6;
+    u = rep - att;
+    mag = rep + att;
+    if (s.g == 0ull) {
+        u = __longlong_as_double(0x7ff0000000000000ll);
+        mag = u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_inclusive_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Device status word bits.
+enum : int {
+    kStatusCellOverflow = 1,
+    kStatusCapacity = 2,
+    kStatusNonFinite = 4,
+    kStatusBadInput = 8,
+    kStatusTimeout = 16,
+};
+
+}  // namespace gcmc

@@ -1,0 +1,468 @@
+// gcmc_energy.cu -- cell-list energies on the compact cell-major layout:
+//   k_trial_energy   energy of many trial points against their 27 cells
+//                    (Algorithms 6 and 7, one warp per trial point);
+//   k_cell_energy    full-system energy, one CTA per home cell (the
+//                    cell-list CalculateTotalEnergy of Sec. 3.1.1);
+//   k_cell_grad      its hand-written gradient (positions, eps, sigma, virial).
+// FP32 mode: pair terms in FP32, per-lane sums compensated (Neumaier), lane
+// and block sums in FP64.  FP64 mode: everything in FP64.
+#include <cmath>
+#include <type_traits>
+
+#include "gcmc_ctx.h"
+
+namespace gcmc {
+
+// Neumaier-compensated float accumulator.
+struct CSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <bool F32>
+struct Acc;
+template <>
+struct Acc<true> {
+    CSum e, a;
+    __device__ __forceinline__ void add(float u, float m)
+    {
+        e.add(u);
+        a.add(m);
+    }
+    __device__ __forceinline__ double ev() const { return e.value(); }
+    __device__ __forceinline__ double av() const { return a.value(); }
+};
+template <>
+struct Acc<false> {
+    double e = 0.0, a = 0.0;
+    __device__ __forceinline__ void add(double u, double m)
+    {
+        e += u;
+        a += m;
+    }
+    __device__ __forceinline__ double ev() const { return e; }
+    __device__ __forceinline__ double av() const { return a; }
+};
+
+// Up to 18 contiguous runs of the compact layout cover the 27 cells around
+// cell (cx, cy, cz): per (dy, dz) row the three x-neighbours are one run, or
+// two when the row wraps around the box.
+struct Runs {
+    int start[18];
+    int end[18];  // inclusive prefix of lengths (flat index space)
+};
+
+__device__ __forceinline__ void row_runs(const int32_t *__restrict__ cs, int T, int cx, int cy, int cz,
+                                         int r, int part, int &b, int &len)
+{
+    int dy = r % 3 - 1, dz = r / 3 - 1;
+    int ny = cy + dy, nz = cz + dz;
+    ny += (ny < 0) ? T : 0;
+    ny -= (ny >= T) ? T : 0;
+    nz += (nz < 0) ? T : 0;
+    nz -= (nz >= T) ? T : 0;
+    const int row = (nz * T + ny) * T;
+    int lo, hi;  // cell range [lo, hi) within the row
+    if (cx >= 1 && cx <= T - 2) {
+        lo = part == 0 ? cx - 1 : 0;
+        hi = part == 0 ? cx + 2 : 0;
+    } else if (cx == 0) {
+        lo = part == 0 ? 0 : T - 1;
+        hi = part == 0 ? 2 : T;
+    } else {
+        lo = part == 0 ? T - 2 : 0;
+        hi = part == 0 ? T : 1;
+    }
+    b = cs[row + lo];
+    len = cs[row + hi] - b;
+    if (hi == lo) len = 0;
+}
+
+// Builds the run table of one warp in shared memory; returns the item count.
+__device__ __forceinline__ int warp_runs(const int32_t *__restrict__ cs, int T, int cx, int cy, int cz,
+                                         Runs &R)
+{
+    const int lane = threadIdx.x & 31;
+    int b = 0, len = 0;
+    if (lane < 18) row_runs(cs, T, cx, cy, cz, lane % 9, lane / 9, b, len);
+    const int inc = warp_inclusive_scan(len);
+    if (lane < 18) {
+        R.start[lane] = b;
+        R.end[lane] = inc;
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, inc, 17);
+}
+
+template <bool F32>
+__device__ __forceinline__ void pair_acc(const uint4 &p, const uint4 &q, uint32_t excl, uint64_t R2,
+                                         int t, const FieldF &ff, const FieldD &fd, Acc<F32> &acc)
+{
+    if (q.w == excl) return;
+    const GridSep s = grid_sep(p, q);
+    if (s.g >= R2) return;
+    const int k = t * kMaxSpecies + (int)tag_species(q.w);
+    if constexpr (F32) {
+        float u, m;
+        lj_f32(s, ff.c4e[k], ff.sig2[k], u, m);
+        acc.add(u, m);
+    } else {
+        double u, m;
+        lj_f64(s, fd.c4e[k], fd.sig2[k], u, m);
+        acc.add(u, m);
+    }
+}
+
+__device__ __forceinline__ uint32_t quantize_dev(double x, double q, bool &ok)
+{
+    const double t = x * q;
+    if (!(t == t) || t > 4.0e18 || t < -4.0e18) {
+        ok = false;
+        return 0u;
+    }
+    return (uint32_t)(unsigned long long)(long long)floor(t);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_trial_energy(
+    const double *__restrict__ pos, const int32_t *__restrict__ species, const int64_t *__restrict__ exclude,
+    int64_t m, const uint4 *__restrict__ cpos, const int32_t *__restrict__ cs, int T, double q, uint64_t R2,
+    int S, const FieldF ff, const FieldD fd, double *__restrict__ out, double *__restrict__ out_abs,
+    int *__restrict__ status)
+{
+    __shared__ Runs runs[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Runs &R = runs[w];
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t k = (int64_t)blockIdx.x * 8 + w; k < m; k += warps) {
+        bool ok = true;
+        uint4 P;
+        P.x = quantize_dev(pos[3 * k + 0], q, ok);
+        P.y = quantize_dev(pos[3 * k + 1], q, ok);
+        P.z = quantize_dev(pos[3 * k + 2], q, ok);
+        const int t = species[k];
+        uint32_t excl = 0xFFFFFFFFu;
+        if (exclude) {
+            const int64_t x = exclude[k];
+            if (x >= 0) excl = make_tag((uint32_t)(x & 0xFFFFFFFFll), (uint32_t)(x >> 32));
+        }
+        if (!ok || t < 0 || t >= S) {
+            if (lane == 0) {
+                out[k] = __longlong_as_double(0x7ff8000000000000ll);
+                if (out_abs) out_abs[k] = out[k];
+                atomicOr(status, kStatusBadInput);
+            }
+            continue;
+        }
+        const int cx = cell_coord(P.x, T), cy = cell_coord(P.y, T), cz = cell_coord(P.z, T);
+        const int total = warp_runs(cs, T, cx, cy, cz, R);
+        Acc<F32> acc;
+        int r = 0;
+        for (int f = lane; f < total; f += 32) {
+            while (f >= R.end[r]) ++r;
+            const int idx = R.start[r] + f - (r ? R.end[r - 1] : 0);
+            const uint4 qv = cpos[idx];
+            pair_acc<F32>(P, qv, excl, R2, t, ff, fd, acc);
+        }
+        const double e = warp_sum(acc.ev());
+        const double a = warp_sum(acc.av());
+        if (lane == 0) {
+            out[k] = e;
+            if (out_abs) out_abs[k] = a;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Full-system energy: one CTA per home cell; the 27 neighbour cells are
+// staged in shared memory, each warp takes home particles, lanes take the
+// staged partners.  Pairs are visited from both sides; the host halves.
+// ---------------------------------------------------------------------------
+constexpr int kStage = 2048;  // staged partners per pass (32 KB)
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ cpos,
+                                                     const int32_t *__restrict__ cs, int T, int64_t ncell,
+                                                     uint64_t R2, const FieldF ff, const FieldD fd,
+                                                     double *__restrict__ partial)
+{
+    __shared__ uint4 stage[kStage];
+    __shared__ Runs runs;
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
+        int total = 0;
+        if (w == 0) total = warp_runs(cs, T, cx, cy, cz, runs);
+        __syncthreads();
+        total = runs.end[17];
+        const int h0 = cs[c], h1 = cs[c + 1];
+        Acc<F32> acc;
+        for (int base = 0; base < total; base += kStage) {
+            const int nst = min(kStage, total - base);
+            for (int f = threadIdx.x; f < nst; f += blockDim.x) {
+                const int g = base + f;
+                int r = 0;
+                while (g >= runs.end[r]) ++r;
+                stage[f] = cpos[runs.start[r] + g - (r ? runs.end[r - 1] : 0)];
+            }
+            __syncthreads();
+            for (int i = h0 + w; i < h1; i += 8) {
+                const uint4 p = cpos[i];
+                const int t = (int)tag_species(p.w);
+                for (int f = lane; f < nst; f += 32) pair_acc<F32>(p, stage[f], p.w, R2, t, ff, fd, acc);
+            }
+            __syncthreads();
+        }
+        double e = warp_sum(acc.ev());
+        if (lane == 0) red[w] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += red[k];
+            partial[c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Deterministic sum of n partials (one block); out[j] for j < width sums
+// partial[i * width + j].
+__global__ void k_sum_partials(const double *__restrict__ partial, int64_t n, int width,
+                               double *__restrict__ out)
+{
+    __shared__ double sh[1024];
+    for (int j = 0; j < width; ++j) {
+        double s = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partial[i * width + j];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[j] = sh[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient.  In grid units (s^2 = sig2 / r_g^2, rep = 4 eps s^12, att = 4 eps s^6):
+//   dE/dx_i = sum_j (-12 rep + 6 att) / r_g^2 * dx_g / h,
+//   r U'(r) = -12 rep + 6 att,
+//   dE/deps_ab (half of each ordered pair) += 2 (s^12 - s^6),
+//   dE/dsigma_ab (same) += (12 rep - 6 att) / (2 sigma_ab).
+// One warp per home particle; the per-cell scalars go to `partial` rows of
+// width 2 + 2 S^2: [E, virial, deps..., dsigma...].
+// ---------------------------------------------------------------------------
+template <bool F32>
+__global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpos, const int32_t *__restrict__ cs,
+                                                   int T, int64_t ncell, uint64_t R2, int S, const FieldF ff,
+                                                   const FieldD fd, double inv_h, const int64_t *__restrict__ d_n,
+                                                   float *__restrict__ dpos, double *__restrict__ partial)
+{
+    using R = typename std::conditional<F32, float, double>::type;
+    constexpr int kW = 2 + 2 * kMaxSpecies * kMaxSpecies;
+    __shared__ Runs runs;
+    __shared__ double red[8][kW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int width = 2 + 2 * S * S;
+    int64_t base_s[kMaxSpecies];
+    {
+        int64_t b = 0;
+        for (int s = 0; s < kMaxSpecies; ++s) {
+            base_s[s] = b;
+            b += (s < S) ? d_n[s] : 0;
+        }
+    }
+    for (int k = threadIdx.x; k < 8 * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
+    __syncthreads();
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
+        if (w == 0) warp_runs(cs, T, cx, cy, cz, runs);
+        __syncthreads();
+        const int total = runs.end[17];
+        const int h0 = cs[c], h1 = cs[c + 1];
+        for (int i = h0 + w; i < h1; i += 8) {
+            const uint4 p = cpos[i];
+            const int t = (int)tag_species(p.w);
+            R fx = 0, fy = 0, fz = 0;
+            CSum sE, sW, sEps[kMaxSpecies], sSig[kMaxSpecies];
+            double dE = 0, dW = 0, dEps[kMaxSpecies] = {}, dSig[kMaxSpecies] = {};
+            int r = 0;
+            for (int g = lane; g < total; g += 32) {
+                while (g >= runs.end[r]) ++r;
+                const uint4 qv = cpos[runs.start[r] + g - (r ? runs.end[r - 1] : 0)];
+                if (qv.w == p.w) continue;
+                const GridSep sp = grid_sep(p, qv);
+                if (sp.g >= R2) continue;
+                const int ts = (int)tag_species(qv.w);
+                const int k = t * kMaxSpecies + ts;
+                const R ddx = (R)sp.dx, ddy = (R)sp.dy, ddz = (R)sp.dz;
+                const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const R c4e = F32 ? (R)ff.c4e[k] : (R)fd.c4e[k];
+                const R sig2 = F32 ? (R)ff.sig2[k] : (R)fd.sig2[k];
+                const R s2 = sig2 / r2;
+                const R s6 = s2 * s2 * s2;
+                const R rep = c4e * s6 * s6, att = c4e * s6;
+                const R rdu = (R)(-12) * rep + (R)6 * att;  // r U'(r)
+                const R coef = rdu / r2;
+                fx += coef * ddx;
+                fy += coef * ddy;
+                fz += coef * ddz;
+                const R ue = (R)0.5 * (rep - att);
+                const R uw = (R)0.5 * rdu;
+                const R ge = (R)2 * (s6 * s6 - s6);
+                const R gs = (R)0.5 * ((R)12 * rep - (R)6 * att);
+                if constexpr (F32) {
+                    sE.add(ue);
+                    sW.add(uw);
+                    sEps[ts].add(ge);
+                    sSig[ts].add(gs);
+                } else {
+                    dE += ue;
+                    dW += uw;
+                    dEps[ts] += ge;
+                    dSig[ts] += gs;
+                }
+            }
+            const double gx = warp_sum((double)fx), gy = warp_sum((double)fy), gz = warp_sum((double)fz);
+            if (lane == 0 && dpos) {
+                const int64_t row = base_s[t] + tag_index(p.w);
+                dpos[3 * row + 0] = (float)(gx * inv_h);
+                dpos[3 * row + 1] = (float)(gy * inv_h);
+                dpos[3 * row + 2] = (float)(gz * inv_h);
+            }
+            const double vE = warp_sum(F32 ? sE.value() : dE);
+            const double vW = warp_sum(F32 ? sW.value() : dW);
+            double ve[kMaxSpecies], vs[kMaxSpecies];
+            for (int ts = 0; ts < S; ++ts) {
+                ve[ts] = warp_sum(F32 ? sEps[ts].value() : dEps[ts]);
+                vs[ts] = warp_sum(F32 ? sSig[ts].value() : dSig[ts]);
+            }
+            if (lane == 0) {
+                red[w][0] += vE;
+                red[w][1] += vW;
+                for (int ts = 0; ts < S; ++ts) {
+                    red[w][2 + t * S + ts] += ve[ts];
+                    red[w][2 + S * S + t * S + ts] += vs[ts];
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < width) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+            partial[c * width + threadIdx.x] = s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 8 * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
+        __syncthreads();
+    }
+}
+
+static unsigned blocks_for(gcmc_ctx *ctx, int64_t work, int per_block)
+{
+    int64_t b = (work + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)ctx->num_sms * 16;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species, const int64_t *exclude,
+                         int64_t m, double *out, double *out_abs)
+{
+    gcmc_status st = make_compact(ctx);
+    if (st != GCMC_OK) return st;
+    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    const unsigned nb = blocks_for(ctx, m, 8);
+    if (ctx->precision == GCMC_FP32)
+        k_trial_energy<true><<<nb, 256, 0, ctx->stream>>>(pos, species, exclude, m, ctx->cpos, ctx->cell_start,
+                                                         ctx->T, ctx->q, ctx->R2, ctx->S, ctx->ff, ctx->fd, out,
+                                                         out_abs, ctx->d_status);
+    else
+        k_trial_energy<false><<<nb, 256, 0, ctx->stream>>>(pos, species, exclude, m, ctx->cpos, ctx->cell_start,
+                                                          ctx->T, ctx->q, ctx->R2, ctx->S, ctx->ff, ctx->fd, out,
+                                                          out_abs, ctx->d_status);
+    ctx->launches += 1;
+    GCMC_CUDA(ctx, cudaGetLastError());
+    int bits = 0;
+    st = read_status(ctx, &bits);
+    if (st != GCMC_OK) return st;
+    if (bits & kStatusBadInput)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_trial_energy: species out of range or coordinate not finite");
+    return GCMC_OK;
+}
+
+gcmc_status total_energy(gcmc_ctx *ctx, double *energy)
+{
+    gcmc_status st = make_compact(ctx);
+    if (st != GCMC_OK) return st;
+    st = ensure_red(ctx, (size_t)ctx->ncell + 8);
+    if (st != GCMC_OK) return st;
+    const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
+    if (ctx->precision == GCMC_FP32)
+        k_cell_energy<true><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2,
+                                                        ctx->ff, ctx->fd, ctx->d_red);
+    else
+        k_cell_energy<false><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2,
+                                                         ctx->ff, ctx->fd, ctx->d_red);
+    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 1, ctx->d_red + ctx->ncell);
+    ctx->launches += 2;
+    GCMC_CUDA(ctx, cudaGetLastError());
+    double e = 0.0;
+    GCMC_CUDA(ctx, cudaMemcpyAsync(&e, ctx->d_red + ctx->ncell, sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    e *= 0.5;
+    ctx->energy = e;
+    ctx->energy_valid = true;
+    GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (energy) *energy = e;
+    return GCMC_OK;
+}
+
+gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
+                        double *virial)
+{
+    gcmc_status st = make_compact(ctx);
+    if (st != GCMC_OK) return st;
+    const int S = ctx->S;
+    const int width = 2 + 2 * S * S;
+    st = ensure_red(ctx, (size_t)ctx->ncell * width + width);
+    if (st != GCMC_OK) return st;
+    const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
+    double *part = ctx->d_red;
+    double *res = ctx->d_red + (size_t)ctx->ncell * width;
+    if (ctx->precision == GCMC_FP32)
+        k_cell_grad<true><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S,
+                                                      ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part);
+    else
+        k_cell_grad<false><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S,
+                                                       ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part);
+    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(part, ctx->ncell, width, res);
+    ctx->launches += 2;
+    GCMC_CUDA(ctx, cudaGetLastError());
+    double h[2 + 2 * kMaxSpecies * kMaxSpecies];
+    GCMC_CUDA(ctx, cudaMemcpyAsync(h, res, width * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (energy) *energy = h[0];
+    if (virial) *virial = h[1];
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            if (deps) deps[a * S + b] = h[2 + a * S + b];
+            if (dsigma) dsigma[a * S + b] = h[2 + S * S + a * S + b] / ctx->sigma[a * kMaxSpecies + b];
+        }
+    return GCMC_OK;
+}
+
+}  // namespace gcmc

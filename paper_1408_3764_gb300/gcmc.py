@@ -1,0 +1,268 @@
+"""Python front end of the GB300 GCMC library.
+
+``Box`` wraps one C-ABI context: PyTorch tensors provide the device memory
+and the CUDA stream, every step of the hot path runs in the library's CUDA
+kernels.  ``cell_list_energy`` is the differentiable full-system energy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MAX_SPECIES, MoveMix, MoveStats, Params, check, load
+
+TRACE_DTYPE = np.dtype([("dU", "<f8"), ("lnA", "<f8"), ("uabs", "<f8"), ("index", "<i4"),
+                        ("type", "u1"), ("species", "u1"), ("accepted", "u1"),
+                        ("flagged", "u1")])
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev(t, dtype, device):
+    t = torch.as_tensor(t, dtype=dtype)
+    return t.to(device).contiguous()
+
+
+@dataclass
+class Mix:
+    """Move mix and thermodynamic state (Algorithm 1, Eqs. 3-5)."""
+    p_disp: float
+    p_ins: float
+    p_del: float
+    max_disp: float
+    beta: float
+    log_z: Sequence[float]
+
+    def to_c(self) -> MoveMix:
+        m = MoveMix()
+        m.p_disp, m.p_ins, m.p_del = self.p_disp, self.p_ins, self.p_del
+        m.max_disp, m.beta = self.max_disp, self.beta
+        lz = list(self.log_z)
+        for s in range(MAX_SPECIES):
+            m.log_z[s] = float(lz[s]) if s < len(lz) else 0.0
+        return m
+
+
+def stats_dict(st: MoveStats, n_species: int) -> dict:
+    return dict(attempted=list(st.attempted), accepted=list(st.accepted), flagged=int(st.flagged),
+                moves_done=int(st.moves_done), energy=float(st.energy),
+                sum_energy=float(st.sum_energy), sum_n=float(st.sum_n),
+                n=[int(st.n[s]) for s in range(n_species)])
+
+
+class Box:
+    """One simulation box on the current CUDA device."""
+
+    def __init__(self, L: float, rc: float, eps, sigma, precision: str = "fp64",
+                 max_particles: int = 0, cell_capacity: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None, device=None):
+        self._lib = load()
+        eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1))
+        sigma = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(-1))
+        S = int(round(np.sqrt(eps.size)))
+        if S * S != eps.size or sigma.size != eps.size:
+            raise ValueError("eps and sigma must be S x S tables")
+        self.S = S
+        self.L, self.rc = float(L), float(rc)
+        self.eps = eps.reshape(S, S).copy()
+        self.sigma = sigma.reshape(S, S).copy()
+        self.precision = precision
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = Params()
+        p.L, p.rc, p.n_species = self.L, self.rc, S
+        p.precision = _lib.FP32 if precision == "fp32" else _lib.FP64
+        p.eps = eps.ctypes.data_as(C.POINTER(C.c_double))
+        p.sigma = sigma.ctypes.data_as(C.POINTER(C.c_double))
+        p.max_particles = int(max_particles)
+        p.cell_capacity = int(cell_capacity)
+        p.reserved = 0
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._lib.gcmc_create(C.byref(p), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                  None, "gcmc_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gcmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def geometry(self) -> dict:
+        g = _lib.Geometry()
+        check(self._lib.gcmc_get_geometry(self._h, C.byref(g)), self._h)
+        return dict(T=g.T, n_cells=g.n_cells, cell_capacity=g.cell_capacity,
+                    max_particles=g.max_particles, cutoff_grid2=g.cutoff_grid2, h=g.h)
+
+    def build_cells(self, pos, species):
+        pos = _dev(pos, torch.float64, self.device).reshape(-1, 3)
+        species = _dev(species, torch.int32, self.device).reshape(-1)
+        if species.numel() != pos.shape[0]:
+            raise ValueError("pos and species disagree in length")
+        with torch.cuda.device(self.device):
+            check(self._lib.gcmc_build_cells(self._h, _ptr(pos), _ptr(species), pos.shape[0]),
+                  self._h, "gcmc_build_cells")
+        self._n_build = pos.shape[0]
+        return self
+
+    def cell_list(self):
+        g = self.geometry()
+        cs = torch.empty(g["n_cells"], dtype=torch.int32, device=self.device)
+        cc = torch.empty_like(cs)
+        order = torch.empty(max(self._n_build, 1), dtype=torch.int32, device=self.device)
+        check(self._lib.gcmc_cell_list(self._h, _ptr(cs), _ptr(cc), _ptr(order)), self._h)
+        return cs, cc, order[: self._n_build]
+
+    def launches(self) -> int:
+        out = np.zeros(1, np.int64)
+        check(self._lib.gcmc_kernel_launches(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
+        return int(out[0])
+
+    def counts(self) -> np.ndarray:
+        out = np.zeros(MAX_SPECIES, np.int64)
+        check(self._lib.gcmc_counts(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
+        return out[: self.S]
+
+    def trial_energy(self, pos, species, exclude=None, with_abs=False):
+        pos = _dev(pos, torch.float64, self.device).reshape(-1, 3)
+        species = _dev(species, torch.int32, self.device).reshape(-1)
+        m = pos.shape[0]
+        ex = None if exclude is None else _dev(exclude, torch.int64, self.device).reshape(-1)
+        out = torch.empty(m, dtype=torch.float64, device=self.device)
+        oabs = torch.empty(m, dtype=torch.float64, device=self.device) if with_abs else None
+        check(self._lib.gcmc_trial_energy(self._h, _ptr(pos), _ptr(species), _ptr(ex), m, _ptr(out),
+                                          _ptr(oabs)), self._h, "gcmc_trial_energy")
+        return (out, oabs) if with_abs else out
+
+    def trial_energy_raw(self, pos: torch.Tensor, species: torch.Tensor, out: torch.Tensor,
+                         exclude: Optional[torch.Tensor] = None, out_abs=None):
+        """No-copy variant on prepared device tensors (used by the benchmark)."""
+        return self._lib.gcmc_trial_energy(self._h, _ptr(pos), _ptr(species), _ptr(exclude),
+                                           pos.shape[0], _ptr(out), _ptr(out_abs))
+
+    def total_energy(self) -> float:
+        e = C.c_double()
+        check(self._lib.gcmc_total_energy(self._h, C.byref(e)), self._h, "gcmc_total_energy")
+        return e.value
+
+    def energy_grad(self, want_pos=True):
+        n = int(self.counts().sum())
+        dpos = torch.empty((max(n, 1), 3), dtype=torch.float32, device=self.device) if want_pos else None
+        S = self.S
+        deps = np.zeros(S * S, np.float64)
+        dsig = np.zeros(S * S, np.float64)
+        e = C.c_double()
+        w = C.c_double()
+        check(self._lib.gcmc_energy_grad(self._h, _ptr(dpos), deps.ctypes.data_as(C.c_void_p),
+                                         dsig.ctypes.data_as(C.c_void_p), C.byref(e), C.byref(w)),
+              self._h, "gcmc_energy_grad")
+        return dict(dpos=dpos[:n] if dpos is not None else None, deps=deps.reshape(S, S),
+                    dsigma=dsig.reshape(S, S), energy=e.value, virial=w.value)
+
+    def run_moves(self, seed: int, first_move: int, n_moves: int, mix: Mix, trace: bool = False,
+                  trace_buf: Optional[torch.Tensor] = None, check_status: bool = True):
+        cm = mix.to_c()
+        st = MoveStats()
+        tb = trace_buf
+        if trace and tb is None:
+            tb = torch.empty((max(n_moves, 1), _lib.TRACE_BYTES), dtype=torch.uint8, device=self.device)
+        rc = self._lib.gcmc_run_moves(self._h, seed, first_move, n_moves, C.byref(cm), C.byref(st),
+                                      _ptr(tb) if (trace or trace_buf is not None) else None)
+        if check_status:
+            check(rc, self._h, "gcmc_run_moves")
+        stats = stats_dict(st, self.S)
+        stats["status"] = rc
+        if trace:
+            arr = tb[:n_moves].cpu().numpy().copy().view(TRACE_DTYPE).reshape(-1)
+            return stats, arr
+        return stats
+
+    def get_state(self):
+        n = self.counts()
+        N = int(n.sum())
+        g = self.geometry()
+        pos = np.zeros((max(N, 1), 3), np.uint32)
+        cc = np.zeros(g["n_cells"], np.int32)
+        refs = np.zeros(max(N, 1), np.uint32)
+        e = C.c_double()
+        check(self._lib.gcmc_get_state(self._h, pos.ctypes.data_as(C.c_void_p),
+                                       cc.ctypes.data_as(C.c_void_p), refs.ctypes.data_as(C.c_void_p),
+                                       C.byref(e)), self._h)
+        return n, pos[:N], cc, refs[:N], e.value
+
+    def restore(self, n_per_species, pos, cell_count, cell_refs, energy=float("nan")):
+        n = np.ascontiguousarray(np.asarray(n_per_species, np.int64))
+        pos = np.ascontiguousarray(np.asarray(pos, np.uint32).reshape(-1, 3))
+        cc = np.ascontiguousarray(np.asarray(cell_count, np.int32))
+        refs = np.ascontiguousarray(np.asarray(cell_refs, np.uint32))
+        check(self._lib.gcmc_set_state(self._h, n.ctypes.data_as(C.c_void_p),
+                                       pos.ctypes.data_as(C.c_void_p), cc.ctypes.data_as(C.c_void_p),
+                                       refs.ctypes.data_as(C.c_void_p), float(energy)), self._h,
+              "gcmc_set_state")
+
+
+def species_major_order(species) -> np.ndarray:
+    """Input indices listed in species-major order (species 0 first, input
+    order within a species): row r of a species-major array belongs to input
+    particle order[r]."""
+    s = np.asarray(species).reshape(-1)
+    return np.argsort(s, kind="stable")
+
+
+class _CellListEnergy(torch.autograd.Function):
+    """Full-system cell-list energy with its hand-written backward (the
+    gradient kernel evaluates dE/dpos, dE/deps and dE/dsigma in one pass)."""
+
+    @staticmethod
+    def forward(ctx, pos, eps, sigma, species, L, rc, precision):
+        box = Box(L, rc, eps.detach().cpu().numpy(), sigma.detach().cpu().numpy(), precision=precision,
+                  device=pos.device if pos.is_cuda else None)
+        box.build_cells(pos.detach().to(torch.float64), species)
+        g = box.energy_grad(want_pos=pos.requires_grad)
+        box.close()
+        sm = torch.as_tensor(species_major_order(species.detach().cpu().numpy()), device=pos.device)
+        dpos = None
+        if g["dpos"] is not None:
+            dpos = torch.empty_like(g["dpos"])
+            dpos[sm] = g["dpos"]
+            dpos = dpos.to(pos.dtype)
+        ctx.save_for_backward(dpos if dpos is not None else torch.empty(0),
+                              torch.as_tensor(g["deps"], dtype=eps.dtype),
+                              torch.as_tensor(g["dsigma"], dtype=sigma.dtype))
+        ctx.has_pos = dpos is not None
+        return torch.tensor(g["energy"], dtype=torch.float64, device=pos.device)
+
+    @staticmethod
+    def backward(ctx, go):
+        dpos, deps, dsig = ctx.saved_tensors
+        gp = (go.to(dpos.dtype) * dpos) if ctx.has_pos else None
+        ge = go.cpu().to(deps.dtype) * deps
+        gs = go.cpu().to(dsig.dtype) * dsig
+        return gp, ge, gs, None, None, None, None
+
+
+def cell_list_energy(pos: torch.Tensor, eps: torch.Tensor, sigma: torch.Tensor, species: torch.Tensor,
+                     L: float, rc: float, precision: str = "fp32") -> torch.Tensor:
+    """E = 1/2 sum_{i != j} U(r_ij) over the cell list, differentiable with
+    respect to pos ([N, 3], CUDA), eps and sigma ([S, S] tables, CPU float64).
+    dE/deps[a][b] is half of the sum over ordered type pairs (a, b), so a
+    symmetric change of both entries sees the full cross-term sum."""
+    return _CellListEnergy.apply(pos, eps, sigma, species, L, rc, precision)

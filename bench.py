@@ -238,6 +238,7 @@ def main():
             chain_times.append(c[0].elapsed_time(c[1]))
         torch.cuda.synchronize()
     launches = box.launches() - launches0
+    counters = box.chain_counters()
     total_ms = sum(times)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -315,7 +316,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single chain"},
                 "chain_moves_per_s": achieved,
                 "acceptance": [st["accepted"][i] / max(1, st["attempted"][i]) for i in range(3)],
-                "final_n": st["n"], "flagged": st["flagged"],
+                "final_n": st["n"], "flagged": st["flagged"], "chain_counters_last_step": counters,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "compare": compare}
         print(json.dumps(line))

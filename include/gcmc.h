@@ -213,6 +213,13 @@ gcmc_status gcmc_get_geometry(gcmc_ctx *ctx, gcmc_geometry *out);
  * diagnostic for launch accounting).  Errors: INVALID_ARG. */
 gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out);
 
+/* Diagnostics of the last gcmc_run_moves (host out, either may be NULL):
+ * refetched = moves whose prefetched neighbour data or particle record was
+ * invalidated by the previous move and loaded again; refined = trials whose
+ * FP32 decision fell inside the error band and were decided in FP64.
+ * Errors: INVALID_ARG. */
+gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char *gcmc_last_error(gcmc_ctx *ctx);
 

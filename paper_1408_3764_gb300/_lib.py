@@ -68,6 +68,7 @@ SIGNATURES = {
     "gcmc_set_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double]),
     "gcmc_get_geometry": (C.c_int, [_vp, C.POINTER(Geometry)]),
     "gcmc_kernel_launches": (C.c_int, [_vp, _vp]),
+    "gcmc_chain_counters": (C.c_int, [_vp, _vp, _vp]),
     "gcmc_last_error": (C.c_char_p, [_vp]),
     "gcmc_version": (C.c_char_p, []),
     "gcmc_probe_latency": (C.c_int, [_vp, C.c_int64, C.POINTER(ProbeResult)]),

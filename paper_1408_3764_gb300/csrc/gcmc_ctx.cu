@@ -1,6 +1,7 @@
 // gcmc_ctx.cu -- the C ABI: context lifetime, parameters, geometry, state
 // import/export and error reporting.  Kernels live in gcmc_cells.cu,
 // gcmc_energy.cu and gcmc_chain.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -132,6 +133,10 @@ gcmc_status gcmc_create(const gcmc_params *p, void *stream, gcmc_ctx **out)
     {
         const double rq = p->rc * ctx->q;
         ctx->R2 = (uint64_t)std::ceil(rq * rq);
+        uint64_t r = (uint64_t)std::sqrt((double)ctx->R2);
+        while (r * r < ctx->R2) ++r;
+        while (r > 0 && (r - 1) * (r - 1) >= ctx->R2) --r;
+        ctx->rcg = (int)std::min<uint64_t>(r, 0x7fffffffull);
     }
     for (int a = 0; a < S; ++a)
         for (int b = 0; b < S; ++b) {
@@ -407,6 +412,14 @@ gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out)
 {
     if (!ctx || !out) return GCMC_ERR_INVALID_ARG;
     *out = ctx->launches;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (refetched) *refetched = ctx->last_refetch;
+    if (refined) *refined = ctx->last_refines;
     return GCMC_OK;
 }
 

@@ -20,6 +20,7 @@ struct gcmc_ctx {
     int T = 3;
     int64_t ncell = 27;
     uint64_t R2 = 0;
+    int rcg = 0;  // smallest integer with rcg^2 >= R2
     int64_t max_particles_req = 0;  // 0 = automatic
     int cap_req = 0;                // 0 = automatic
     int64_t maxN = 0;               // per species, as allocated
@@ -60,6 +61,8 @@ struct gcmc_ctx {
     double energy = 0.0;
     bool energy_valid = false;
     int64_t launches = 0;  // kernels this context has launched
+    int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
+    int64_t last_refines = 0;  // chain trials decided in FP64 after the FP32 band test (last run)
 
     std::string err;
 };

@@ -136,6 +136,12 @@ class Box:
         check(self._lib.gcmc_kernel_launches(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
         return int(out[0])
 
+    def chain_counters(self) -> dict:
+        out = np.zeros(2, np.int64)
+        check(self._lib.gcmc_chain_counters(self._h, out[0:].ctypes.data_as(C.c_void_p),
+                                            out[1:].ctypes.data_as(C.c_void_p)), self._h)
+        return dict(refetched=int(out[0]), refined=int(out[1]))
+
     def counts(self) -> np.ndarray:
         out = np.zeros(MAX_SPECIES, np.int64)
         check(self._lib.gcmc_counts(self._h, out.ctypes.data_as(C.c_void_p)), self._h)

@@ -301,6 +301,24 @@ def test_explicit_capacity_overflow_is_reported():
     assert cc.max() <= 8 and cc.sum() == cnt.sum()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L,max_disp", [(13.0, 3.0), (10.4, 2.9), (16.0, 5.5)])
+def test_chain_parity_far_displacements(precision, L, max_disp):
+    """Displacements longer than a cell edge (T = 5, 4, 6): the old and new
+    neighbourhoods are visited separately; decisions still match move by move."""
+    n = int(0.45 * L ** 3)
+    pos = _relaxed(n, L, 77, dmin=0.8)
+    o, _, b = _pair(L, 2.5, [[1.0]], [[1.0]], pos, np.zeros(n, np.int32), precision)
+    o.set_energy(o.total_energy())
+    args = (0.6, 0.2, 0.2, max_disp, 1 / 1.2, [-2.7])
+    to, _ = o.run_moves(13, 0, 20_000, *args, tol=TOL[precision])
+    sg, tg = b.run_moves(13, 0, 20_000, Mix(*args), trace=True)
+    assert _compare_traces(tg, to, TOL[precision]) == len(to)
+    st_o, st_g = o.state(), b.get_state()
+    for x, y in zip(st_o, st_g[:4]):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_chain_parity_full_size_c2(precision):
     """131,072 particles, rho 0.6, rc 3: 10^5 moves of the full-size workload,

@@ -1,30 +1,35 @@
 // gcmc_chain.cu -- the grand canonical Markov chain run entirely on the
-// device (Sec. 2 and Algorithm 1; the optimised code of Sec. 3.3.4 runs many
-// moves per launch, here one launch runs all of them).
+// device (Sec. 2 and Algorithm 1), with the concurrent evaluation of
+// upcoming moves that the paper lists as future work (Sec. 5: run multiple
+// moves concurrently), here inside one CTA.
 //
-// One CTA owns one chain.  The chain is a strictly sequential sequence of
-// moves, so the design goal is a short dependent path per move.  On GB300 a
-// dependent FP64 operation costs ~100 cycles and an L2 round trip ~300, so:
+// One CTA owns one chain.  Its warps have three roles:
 //
-//  * random words: Philox4x32-10 blocks and an FP32 log of the acceptance
-//    uniform are precomputed 32 moves at a time into a shared-memory ring;
-//  * software pipeline: while move m is evaluated, the neighbour-cell
-//    contents of move m+1 are loaded into registers and the particle record
-//    of move m+2 is fetched.  After m's decision both are validated against
-//    what m changed (cells touched, N changed, same particle); on conflict
-//    they are re-fetched, so every move sees exactly the state the
-//    sequential chain would;
-//  * the 27 neighbour cells (up to 46 for a displacement that changes cell:
-//    the union of both neighbourhoods, each cell flagged old/new) are
-//    flattened into one item list spread over all threads;
-//  * pair sums are float-float (TwoSum) in registers and shuffles; the
-//    Metropolis test runs in FP32 with an explicit error band, and a trial
-//    inside the band is recomputed entirely in FP64 (pair terms, sums and
-//    log), so every decision equals the FP64 rule's;
-//  * two CTA barriers per move: after the partial sums, and after warp 0 has
-//    decided and applied the update (Sec. 3.2.5: swap-with-last removal,
-//    append, species index refill).
-// The cell counters live in shared memory (uint16) for the whole launch.
+//  * evaluators (warps 1..EW): warp w evaluates moves w-1, w-1+EW, ...
+//    Each evaluation is speculative: it reads the configuration as it
+//    stands when the evaluation starts (after `committed` moves) and
+//    produces the trial (particle, old/new position, cells), its energy
+//    change dU (27 neighbour cells, Algorithms 6 and 7; the union of both
+//    neighbourhoods for a displacement that changes cell), the error scale
+//    uabs, and the slots the update will need.  Pair terms are FP32 (or FP64)
+//    from exact integer separations; sums are float-float;
+//  * the committer (warp 0) takes the moves strictly in order.  A move is
+//    valid when no move committed after its evaluation started touched one
+//    of its cells, changed N (which selects the particle of a displacement
+//    or deletion) or wrote its particle's record; otherwise the committer
+//    evaluates it again against the current configuration.  It then takes
+//    the Metropolis decision (Eqs. 3-5, textbook sign of mu) in FP32 with an
+//    explicit error band -- a trial inside the band is recomputed entirely in
+//    FP64 -- and applies an accepted move (Sec. 3.2.5: swap-with-last
+//    removal, append, species index refill).  Every decision is therefore
+//    the one the sequential chain takes;
+//  * the keeper (last warp) keeps the FP64 running energy, the averages, the
+//    counters and the trace, and refills the ring of Philox4x32-10 words.
+//
+// Warps hand work to each other through shared-memory rings and counters
+// with block-scope fences; every wait is bounded and sets a timeout status
+// instead of hanging.  Cell counters live in shared memory (uint16) for the
+// whole launch; particle data stays in the padded cell-major layout in L2.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -43,14 +48,15 @@ struct ChainOut {
     double sum_n;
     long long n[kMaxSpecies];
     int status;
-    int refetch;        // moves whose prefetched data had to be re-fetched
-    long long refines;  // trials decided in FP64 after the FP32 band test
+    int pad;
+    long long reevaluated;  // moves evaluated again by the committer
+    long long refines;      // trials decided in FP64 after the FP32 band test
 };
 
 struct ChainArgs {
     uint64_t seed;
     uint64_t first;
-    long long n_moves;
+    int n_moves;
     uint32_t chain;
     int T;
     int ncell;
@@ -58,14 +64,15 @@ struct ChainArgs {
     long long maxN;
     int S;
     unsigned long long R2;
-    int rcg;        // smallest integer with rcg^2 >= R2 (per-axis pre-filter)
+    int rcg;  // smallest integer with rcg^2 >= R2 (per-axis pre-filter)
+    float r2lo, r2hi;  // FP32 squared distances clearly inside / outside the cutoff
     unsigned long long thr_disp, thr_ins;
     uint32_t span;  // 2 D + 1 grid steps
     int D;          // displacement half-width in grid steps
     double beta, lnV;
     double logz[kMaxSpecies];
-    double tol;     // relative tolerance that defines "near the threshold"
-    float lnzv_f[kMaxSpecies];  // (float)(ln z_s + ln V)
+    double tol;  // relative tolerance that defines "near the threshold"
+    float lnzv_f[kMaxSpecies];
     FieldF ff;
     FieldD fd;
     uint4 *cell_pos;
@@ -77,11 +84,11 @@ struct ChainArgs {
     ChainOut *out;
 };
 
-constexpr int kRing = 64;      // moves of precomputed words
-constexpr int kRefill = 32;    // refilled this many at a time
+constexpr int kRS = 32;       // move slots in flight (logs and book entries too)
+constexpr int kRW = 128;      // words ring
+constexpr int kFill = 32;     // words filled per keeper round
+constexpr long long kSpinMax = 1ll << 27;
 constexpr uint32_t kOld = 1u, kNew = 2u;
-
-__device__ __forceinline__ long long llmin_(long long x, long long y) { return x < y ? x : y; }
 
 // ---------------------------------------------------------------- float-float
 struct FF {
@@ -118,27 +125,17 @@ __device__ __forceinline__ FF ff_warp_sum(FF v)
 }
 
 // ---------------------------------------------------------------- trials
-struct Choice {
-    int idx;                // particle index (-1: none; insertions get theirs at decision)
-    unsigned type : 2;      // 0 displacement, 1 insertion, 2 deletion
-    unsigned s : 4;         // species
-    unsigned possible : 1;
-};
-
 struct Trial {
-    Choice c;
-    uint4 Po, Pn;          // old / new position; Po.w = the particle's tag
-    int co, cn;            // cells (-1 when absent)
-    unsigned px : 10, py : 10, pz : 10;  // primary neighbourhood centre (old cell; new for insertions)
-    unsigned cross : 1;    // displacement that changes cell
-    unsigned far : 1;      // ... by more than one cell along some axis
+    uint4 Po, Pn;     // old / new position; Po.w = the particle's tag (~0 for insertions)
+    int co, cn;       // cells (-1 when absent)
+    int idx;          // particle index (-1: none; insertions: filled at decision)
+    unsigned px : 10, py : 10, pz : 10;  // primary neighbourhood centre
+    unsigned possible : 1, cross : 1;
     unsigned qx : 10, qy : 10, qz : 10;  // new cell (== primary unless the cell changes)
-    unsigned fpri : 2;     // flags of the primary neighbourhood's cells
+    unsigned far : 1, pad : 1;
+    unsigned type : 2, s : 4, fpri : 2;
 };
 
-// Up to 4 distinct periodic coordinates along one axis, each flagged old/new:
-// the union of {p-1, p, p+1} (flags fpri, or kOld for a cell-changing move)
-// and {q-1, q, q+1} (kNew) for a cell-changing move.
 struct AxisList {
     int v[4];
     uint32_t f[4];
@@ -147,10 +144,10 @@ struct AxisList {
 
 __device__ __forceinline__ int wrapc(int x, int T) { return x < 0 ? x + T : (x >= T ? x - T : x); }
 
-__device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t fpri, int T)
+// {p-1, p, p+1} flagged f0, united with {q-1, q, q+1} flagged kNew when cross
+__device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t f0, int T)
 {
     AxisList L;
-    const uint32_t f0 = cross ? kOld : fpri;
     L.v[0] = wrapc(p - 1, T);
     L.v[1] = p;
     L.v[2] = wrapc(p + 1, T);
@@ -159,7 +156,6 @@ __device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t 
     L.f[3] = 0;
     L.n = 3;
     if (cross) {
-        // at most one of q-1, q, q+1 lies outside {p-1, p, p+1} (|q - p| <= 1)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int w = wrapc(q + k - 1, T);
@@ -167,7 +163,7 @@ __device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t 
             L.f[0] |= h0 ? kNew : 0u;
             L.f[1] |= h1 ? kNew : 0u;
             L.f[2] |= h2 ? kNew : 0u;
-            if (!(h0 || h1 || h2)) {
+            if (!(h0 || h1 || h2)) {  // at most one value per axis (|q - p| <= 1)
                 L.v[3] = w;
                 L.f[3] = kNew;
                 L.n = 4;
@@ -183,56 +179,74 @@ __device__ __forceinline__ bool near1(int d, int T)
     return d <= 1 || d == T - 1;
 }
 
-// whether the cell at (x, y, z) is among the trial's work cells
 __device__ __forceinline__ bool in_work(const Trial &t, int x, int y, int z, int T)
 {
-    if (!t.c.possible) return false;
-    if (near1(x - t.px, T) && near1(y - t.py, T) && near1(z - t.pz, T)) return true;
-    return t.cross && near1(x - t.qx, T) && near1(y - t.qy, T) && near1(z - t.qz, T);
+    if (!t.possible) return false;
+    if (near1(x - (int)t.px, T) && near1(y - (int)t.py, T) && near1(z - (int)t.pz, T)) return true;
+    return t.cross && near1(x - (int)t.qx, T) && near1(y - (int)t.qy, T) && near1(z - (int)t.qz, T);
 }
 
-template <int NT>
-struct __align__(16) ChainSmem {
-    uint32_t w[kRing][8];
-    float lnu[kRing];
-    float red_hi[NT / 32], red_lo[NT / 32], red_a[NT / 32];
-    double red_d[NT / 32], red_da[NT / 32];
-    long long n[kMaxSpecies];
-    float ln_n[kMaxSpecies];   // ln N_s
-    float ln_n1[kMaxSpecies];  // ln (N_s + 1)
-    uint4 last_val;            // last particle of the old cell (swap-with-last)
-    int self_slot;             // slot of the trial particle in its cell
-    int decision;              // bit0 accept, bit1 stop, bit2 refine in FP64
-    int mod_x[3], mod_y[3], mod_z[3];  // cells the accepted move changed (x = -1: none)
-    int mod_ids[3];            // particle records it wrote: (s << 24) | index
-    int nchanged;              // N changed
+// cells of one (y, z) row of a trial's neighbourhood: up to 4, flagged
+struct Row {
+    int cell[4];
+    uint32_t fl[4];
+    int p1, p2, p3, tot;
 };
 
-// Philox words and FP32 ln(u) for moves [m0, m0 + count) (count <= 32)
-template <int NT>
-__device__ __forceinline__ void fill_ring(ChainSmem<NT> &sh, const ChainArgs &a, uint64_t m0, int count)
-{
-    const int t = threadIdx.x;
-    if (t < 2 * count) {
-        const int k = t >> 1, half = t & 1;
-        const uint64_t m = m0 + (uint64_t)k;
-        const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        const uint4 r = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, (uint32_t)half), key);
-        const int slot = (int)(m % kRing);
-        sh.w[slot][4 * half + 0] = r.x;
-        sh.w[slot][4 * half + 1] = r.y;
-        sh.w[slot][4 * half + 2] = r.z;
-        sh.w[slot][4 * half + 3] = r.w;
-        if (half == 1) {
-            const uint64_t k53 = ((uint64_t)(r.z >> 5) << 26) | (uint64_t)(r.w >> 6);
-            float l;
-            if (k53 == 0) l = -INFINITY;                                   // u = 0: always accept
-            else if (k53 < (1ull << 27)) l = __int_as_float(0x7fc00000);  // u < 2^-26: decide in FP64
-            else l = logf((float)((double)k53 * 1.1102230246251565404e-16));
-            sh.lnu[slot] = l;
-        }
-    }
-}
+// ---------------------------------------------------------------- shared state
+struct WordRec {
+    uint32_t w[8];
+    float lnu;  // FP32 ln(u) of the acceptance uniform; NaN: decide in FP64
+    int pad[3];
+};
+
+struct Slot {  // evaluator -> committer
+    Trial t;
+    uint4 last_val;
+    float hi, lo, uab;
+    int self_slot;
+    int c0;
+    int ready;  // move + 1 when filled
+};
+
+struct LogRec {  // committer -> evaluation validity
+    int flags;   // bit0 accepted, bit1 N changed
+    int mx[3], my[3], mz[3];
+    int ids[3];  // (s << 24) | index of records written
+};
+
+struct BookRec {  // committer -> keeper
+    double dU, lnA;
+    float uab;
+    int fin;      // bit0 accepted
+    int type, sp, index;
+    int possible;
+    int refined;  // bit0 near threshold, bit1 decided in FP64, bit2 evaluated again
+    int pad0;
+    long long ns;  // N_s before the move
+    int ready;
+    int pad1;
+};
+
+struct __align__(16) Shared {
+    WordRec words[kRW];
+    Slot slots[kRS];
+    LogRec logs[kRS];
+    BookRec book[kRS];
+    long long n[kMaxSpecies];
+    float ln_n[kMaxSpecies];
+    float ln_n1[kMaxSpecies];
+    int ns_ring[kRS][kMaxSpecies];  // N_s after c commits, at [c % kRS]
+    int committed;  // moves committed
+    int filled;     // words available for moves < filled
+    int booked;     // moves the keeper has processed
+    int stop;       // the committer stopped: no further moves are taken
+    int status;
+    int dummy;
+};
+
+__device__ __forceinline__ int vload(const int &x) { return *(volatile const int *)&x; }
+__device__ __forceinline__ void vstore(int &x, int v) { *(volatile int *)&x = v; }
 
 template <bool F32>
 __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const ChainArgs &a, int k, float sign,
@@ -261,121 +275,97 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
     }
 }
 
-constexpr int kWarpsW = 8;     // worker warps
-constexpr int kRowItems = 2;   // prefetched items per lane and row
-constexpr int kRowsW = 2;      // rows per worker warp (a trial has at most 16)
-constexpr int kSlots = kRowItems * kRowsW;
-
-// The cells of one (y, z) row of a trial: up to 4, with flags and counts.
-struct Row {
-    int cell[4];
-    uint32_t fl[4];
-    int p1, p2, p3, tot;  // item prefix boundaries
-};
-
-template <bool F32, int NT>
+// ---------------------------------------------------------------- the chain
+template <bool F32>
 struct Chain {
     const ChainArgs &a;
-    ChainSmem<NT> &sh;
+    Shared &sh;
     uint16_t *cnt;
-    int tid, lane, warp, T;
+    int lane, warp, T;
     uint32_t uT;
 
-    __device__ Chain(const ChainArgs &a_, ChainSmem<NT> &sh_, uint16_t *cnt_) : a(a_), sh(sh_), cnt(cnt_)
+    __device__ Chain(const ChainArgs &a_, Shared &sh_, uint16_t *cnt_) : a(a_), sh(sh_), cnt(cnt_)
     {
-        tid = threadIdx.x;
-        lane = tid & 31;
-        warp = tid >> 5;
+        lane = threadIdx.x & 31;
+        warp = threadIdx.x >> 5;
         T = a.T;
         uT = (uint32_t)a.T;
     }
 
-    __device__ __forceinline__ const uint32_t *words(long long mm) const
+    __device__ __forceinline__ const WordRec &words(int m) const
     {
-        return sh.w[(int)((a.first + (uint64_t)mm) % kRing)];
+        return sh.words[(int)((a.first + (uint64_t)m) % kRW)];
     }
 
-    __device__ __forceinline__ Choice choose(long long mm) const
+    // the trial of move m given the particle counts ns[] (warp-uniform)
+    __device__ __forceinline__ Trial make_trial(int m, const int *ns) const
     {
-        Choice c;
-        const uint32_t *w = words(mm);
-        c.type = (w[0] < a.thr_disp) ? 0 : ((w[0] < a.thr_ins) ? 1 : 2);
-        c.possible = 1;
-        c.s = 0;
-        c.idx = -1;
-        if (c.type == 0) {
-            long long N = 0;
-#pragma unroll
-            for (int q = 0; q < kMaxSpecies; ++q) N += sh.n[q];
+        const WordRec &W = words(m);
+        Trial t;
+        const uint32_t w0 = W.w[0];
+        const int type = (w0 < a.thr_disp) ? 0 : ((w0 < a.thr_ins) ? 1 : 2);
+        t.type = type;
+        t.possible = 1;
+        t.cross = 0;
+        t.far = 0;
+        t.pad = 0;
+        int s = 0, idx = -1;
+        if (type == 0) {
+            int N = 0;
+            for (int q = 0; q < a.S; ++q) N += ns[q];
             if (N == 0) {
-                c.possible = 0;
+                t.possible = 0;
             } else {
-                long long k = (long long)__umulhi(w[1], (uint32_t)N);
-                int s = 0;
-                while (k >= sh.n[s]) {
-                    k -= sh.n[s];
+                int k = (int)__umulhi(W.w[1], (uint32_t)N);
+                while (k >= ns[s]) {
+                    k -= ns[s];
                     ++s;
                 }
-                c.s = s;
-                c.idx = (int)k;
+                idx = k;
             }
         } else {
-            c.s = (int)__umulhi(w[5], (uint32_t)a.S);
-            if (c.type == 2) {
-                if (sh.n[c.s] == 0) c.possible = 0;
-                else c.idx = (int)__umulhi(w[1], (uint32_t)sh.n[c.s]);
+            s = (int)__umulhi(W.w[5], (uint32_t)a.S);
+            if (type == 2) {
+                if (ns[s] == 0) t.possible = 0;
+                else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
             }
         }
-        return c;
-    }
-
-    __device__ __forceinline__ static bool needs_rec(const Choice &c) { return c.possible && c.type != 1; }
-
-    __device__ __forceinline__ uint4 load_rec(const Choice &c) const
-    {
-        return needs_rec(c) ? a.pos_by_id[(long long)c.s * a.maxN + c.idx] : make_uint4(0, 0, 0, 0);
-    }
-
-    __device__ __forceinline__ Trial finish(const Choice &c, uint4 rec, long long mm) const
-    {
-        Trial t;
-        t.c = c;
-        const uint32_t *w = words(mm);
+        t.s = s;
+        t.idx = idx;
         t.Po = make_uint4(0, 0, 0, 0xFFFFFFFFu);
         t.Pn = make_uint4(0, 0, 0, 0);
         t.co = t.cn = -1;
         t.px = t.py = t.pz = t.qx = t.qy = t.qz = 0;
-        t.cross = 0;
-        t.far = 0;
         t.fpri = 0;
-        if (!c.possible) return t;
-        if (c.type != 1) {
+        if (!t.possible) return t;
+        if (type != 1) {
+            const uint4 rec = a.pos_by_id[(long long)s * a.maxN + idx];
             t.Po = rec;
             t.px = cell_coord(rec.x, uT);
             t.py = cell_coord(rec.y, uT);
             t.pz = cell_coord(rec.z, uT);
-            t.co = (t.pz * T + t.py) * T + t.px;
+            t.co = ((int)t.pz * T + (int)t.py) * T + (int)t.px;
         }
-        if (c.type == 0) {
-            t.Pn.x = rec.x + (uint32_t)((int)__umulhi(w[2], a.span) - a.D);
-            t.Pn.y = rec.y + (uint32_t)((int)__umulhi(w[3], a.span) - a.D);
-            t.Pn.z = rec.z + (uint32_t)((int)__umulhi(w[4], a.span) - a.D);
-            t.Pn.w = rec.w;
-        } else if (c.type == 1) {
-            t.Pn = make_uint4(w[2], w[3], w[4], 0u);
+        if (type == 0) {
+            t.Pn.x = t.Po.x + (uint32_t)((int)__umulhi(W.w[2], a.span) - a.D);
+            t.Pn.y = t.Po.y + (uint32_t)((int)__umulhi(W.w[3], a.span) - a.D);
+            t.Pn.z = t.Po.z + (uint32_t)((int)__umulhi(W.w[4], a.span) - a.D);
+            t.Pn.w = t.Po.w;
+        } else if (type == 1) {
+            t.Pn = make_uint4(W.w[2], W.w[3], W.w[4], 0u);
         }
-        if (c.type != 2) {
+        if (type != 2) {
             t.qx = cell_coord(t.Pn.x, uT);
             t.qy = cell_coord(t.Pn.y, uT);
             t.qz = cell_coord(t.Pn.z, uT);
-            t.cn = (t.qz * T + t.qy) * T + t.qx;
+            t.cn = ((int)t.qz * T + (int)t.qy) * T + (int)t.qx;
         }
-        if (c.type == 1) {
+        if (type == 1) {
             t.px = t.qx;
             t.py = t.qy;
             t.pz = t.qz;
             t.fpri = kNew;
-        } else if (c.type == 2) {
+        } else if (type == 2) {
             t.qx = t.px;
             t.qy = t.py;
             t.qz = t.pz;
@@ -383,60 +373,74 @@ struct Chain {
         } else {
             t.cross = (t.co != t.cn) ? 1 : 0;
             t.fpri = t.cross ? kOld : (kOld | kNew);
-            t.far = t.cross && !(near1(t.px - t.qx, T) && near1(t.py - t.qy, T) && near1(t.pz - t.qz, T));
+            t.far = t.cross && !(near1((int)t.px - (int)t.qx, T) && near1((int)t.py - (int)t.qy, T) &&
+                                 near1((int)t.pz - (int)t.qz, T));
         }
         return t;
     }
 
     __device__ __forceinline__ int nrows(const Trial &t) const
     {
-        if (!t.c.possible) return 0;
+        if (!t.possible) return 0;
         if (!t.cross) return 9;
-        if (t.far) return 18;  // the two neighbourhoods visited separately
+        if (t.far) return 18;
         const int ny = (t.py == t.qy) ? 3 : (T == 3 ? 3 : 4);
         const int nz = (t.pz == t.qz) ? 3 : (T == 3 ? 3 : 4);
         return ny * nz;
     }
 
-    // the cells of row r (0 <= r < nrows) with their flags and counts.  A
-    // near cell-changing displacement visits the union of both
-    // neighbourhoods once (cells flagged old and/or new); a far one visits
-    // the old neighbourhood (rows 0-8, old) and the new one (rows 9-17, new).
+    // Row r of the neighbourhood: a near cell-changing displacement visits
+    // the union of both neighbourhoods once (cells flagged old and/or new); a
+    // far one visits the old neighbourhood (rows 0-8) and the new (9-17).
     __device__ __forceinline__ Row row(const Trial &t, int r) const
     {
+        Row R;
+        if (!t.cross) {  // the common case: 3 x 3 rows of 3 cells
+            const int iz = (r * 11) >> 5, iy = r - 3 * iz;  // r / 3 for r < 16
+            const int y = wrapc((int)t.py + iy - 1, T), z = wrapc((int)t.pz + iz - 1, T);
+            const int base = (z * T + y) * T;
+            R.cell[0] = base + wrapc((int)t.px - 1, T);
+            R.cell[1] = base + (int)t.px;
+            R.cell[2] = base + wrapc((int)t.px + 1, T);
+            R.cell[3] = 0;
+            R.fl[0] = R.fl[1] = R.fl[2] = t.fpri;
+            R.fl[3] = 0;
+            const int n0 = cnt[R.cell[0]], n1 = cnt[R.cell[1]], n2 = cnt[R.cell[2]];
+            R.p1 = n0;
+            R.p2 = n0 + n1;
+            R.p3 = R.p2 + n2;
+            R.tot = R.p3;
+            return R;
+        }
         AxisList X, Y, Z;
         if (t.far) {
             const bool nw = r >= 9;
             r = nw ? r - 9 : r;
             const uint32_t fl = nw ? kNew : kOld;
-            X = axis_list(nw ? t.qx : t.px, 0, 0, fl, T);
-            Y = axis_list(nw ? t.qy : t.py, 0, 0, fl, T);
-            Z = axis_list(nw ? t.qz : t.pz, 0, 0, fl, T);
+            X = axis_list(nw ? (int)t.qx : (int)t.px, 0, 0, fl, T);
+            Y = axis_list(nw ? (int)t.qy : (int)t.py, 0, 0, fl, T);
+            Z = axis_list(nw ? (int)t.qz : (int)t.pz, 0, 0, fl, T);
         } else {
-            X = axis_list(t.px, t.qx, t.cross, t.fpri, T);
-            Y = axis_list(t.py, t.qy, t.cross, t.fpri, T);
-            Z = axis_list(t.pz, t.qz, t.cross, t.fpri, T);
+            X = axis_list(t.px, t.qx, 1, kOld, T);
+            Y = axis_list(t.py, t.qy, 1, kOld, T);
+            Z = axis_list(t.pz, t.qz, 1, kOld, T);
         }
-        // r < 16: r / 3 == (r * 11) >> 5, r / 4 == r >> 2
         const int iz = (Y.n == 4) ? (r >> 2) : ((r * 11) >> 5);
         const int iy = r - iz * Y.n;
         uint32_t fyz = 0;
         int vy = 0, vz = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 4; ++j)
             if (j == iy) {
                 fyz = Y.f[j];
                 vy = Y.v[j];
             }
-        }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 4; ++j)
             if (j == iz) {
                 fyz &= Z.f[j];
                 vz = Z.v[j];
             }
-        }
-        Row R;
         const int base = (vz * T + vy) * T;
         int n[4];
 #pragma unroll
@@ -453,120 +457,226 @@ struct Chain {
         return R;
     }
 
-    __device__ __forceinline__ void locate(const Row &R, int f, int &cell, int &slot, uint32_t &fl) const
+    // One item (a particle of a work cell) against the trial's old and/or new
+    // position, branch-free so that the items of a lane interleave: every
+    // pair term is computed and then masked by the cutoff test.  The cutoff
+    // is decided on the FP32 squared distance except inside a thin band
+    // around rc^2, where the exact integer squared distance decides.
+    template <int SIDES>
+    __device__ __forceinline__ void item32(const Trial &t, const float3 &dp, const uint4 &q, bool valid, uint32_t fl,
+                                           float &acc, float &mag) const
     {
-        const int k = (f >= R.p1) + (f >= R.p2) + (f >= R.p3);
-        const int b = k == 0 ? 0 : (k == 1 ? R.p1 : (k == 2 ? R.p2 : R.p3));
-        cell = k == 0 ? R.cell[0] : (k == 1 ? R.cell[1] : (k == 2 ? R.cell[2] : R.cell[3]));
-        fl = k == 0 ? R.fl[0] : (k == 1 ? R.fl[1] : (k == 2 ? R.fl[2] : R.fl[3]));
-        slot = f - b;
+        const bool use = valid && (q.w != t.Po.w);
+        const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
+        const float c4e = a.ff.c4e[kk], sig2 = a.ff.sig2[kk];
+        // SIDES 1: the old position only (deletion); 2: the new only
+        // (insertion); 3: both (displacement)
+        const uint4 &P0 = (SIDES == 2) ? t.Pn : t.Po;
+        const int dx = (int)(P0.x - q.x), dy = (int)(P0.y - q.y), dz = (int)(P0.z - q.z);
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+#pragma unroll
+        for (int side = 0; side < (SIDES == 3 ? 2 : 1); ++side) {
+            int ex = dx, ey = dy, ez = dz;
+            float gx = fx, gy = fy, gz = fz;
+            if (SIDES == 3 && side == 1) {
+                ex = (int)(t.Pn.x - q.x);
+                ey = (int)(t.Pn.y - q.y);
+                ez = (int)(t.Pn.z - q.z);
+                gx = fx + dp.x;
+                gy = fy + dp.y;
+                gz = fz + dp.z;
+            }
+            const uint32_t need = (SIDES == 3) ? (side ? kNew : kOld) : (SIDES == 2 ? kNew : kOld);
+            const float r2f = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            bool in = use && (fl & need) && (r2f < a.r2lo);
+            if (use && (fl & need) && r2f >= a.r2lo && r2f <= a.r2hi) {
+                const unsigned long long g = (unsigned long long)((long long)ex * ex) +
+                                             (unsigned long long)((long long)ey * ey) +
+                                             (unsigned long long)((long long)ez * ez);
+                in = g < a.R2;
+            }
+            const float r2 = in ? r2f : 1e30f;
+            const float s2 = __fdividef(sig2, r2);
+            const float s6 = s2 * s2 * s2;
+            const float cs = c4e * s6;
+            float u = cs * (s6 - 1.f), m = cs * (s6 + 1.f);
+            if (ex == 0 && ey == 0 && ez == 0) u = m = __int_as_float(0x7f800000);
+            const bool neg = (SIDES == 1) || (SIDES == 3 && side == 0);
+            acc += in ? (neg ? -u : u) : 0.f;
+            mag += in ? m : 0.f;
+        }
     }
 
-    __device__ __forceinline__ int meta_of(const Trial &t, int cell, int slot, uint32_t fl) const
+    // Energy change of a trial over rows r0, r0 + rstep, ... of its
+    // neighbourhood (one warp).  P32: FP32 pair terms, plain FP32 sums per
+    // lane, float-float across lanes; else FP64 throughout.  Also finds the
+    // trial particle's slot and the old cell's last particle.
+    template <bool P32>
+    __device__ __forceinline__ void energy(const Trial &t, int r0, int rstep, FF &e, float &ua, double &de,
+                                           double &da, int &self_slot, uint4 &last_val, int &found_last) const
     {
-        const int last = (cell == t.co) && (slot == (int)cnt[cell] - 1);
-        return slot | ((int)fl << 16) | ((cell == t.co) ? (1 << 18) : 0) | (last ? (1 << 19) : 0);
-    }
-
-    // loads this warp's prefetched items (rows warp, warp + 8; 2 per lane each)
-    __device__ __forceinline__ void gather(const Trial &t, uint4 *it, int *meta) const
-    {
+        e = FF{0.f, 0.f};
+        ua = 0.f;
+        de = da = 0.0;
+        float acc = 0.f, mag = 0.f;
+        // displacement in grid steps (exact integers, then one rounding)
+        const float3 dp = make_float3((float)(int)(t.Pn.x - t.Po.x), (float)(int)(t.Pn.y - t.Po.y),
+                                      (float)(int)(t.Pn.z - t.Po.z));
+        int my_self = -1, my_last = 0;
+        uint4 my_lv = make_uint4(0, 0, 0, 0);
         const int rows = nrows(t);
+        for (int r = r0; r < rows; r += 2 * rstep) {
+            const Row R0 = row(t, r);
+            Row R1;
+            R1.tot = 0;
+            if (r + rstep < rows) R1 = row(t, r + rstep);
+            // up to 4 loads (2 rows x 2 items per lane) in flight together
+            uint4 q[4];
+            int cl[4], sl[4];
+            uint32_t fl[4];
 #pragma unroll
-        for (int rr = 0; rr < kRowsW; ++rr) {
-            const int r = warp + rr * kWarpsW;
+            for (int k = 0; k < 4; ++k) {
+                const Row &R = (k < 2) ? R0 : R1;
+                const int f = lane + 32 * (k & 1);
+                cl[k] = -1;
+                sl[k] = 0;
+                fl[k] = 0;
+                q[k] = make_uint4(0, 0, 0, 0xFFFFFFFEu);
+                if (f < R.tot) {
+                    const int j = (f >= R.p1) + (f >= R.p2) + (f >= R.p3);
+                    const int b = j == 0 ? 0 : (j == 1 ? R.p1 : (j == 2 ? R.p2 : R.p3));
+                    cl[k] = j == 0 ? R.cell[0] : (j == 1 ? R.cell[1] : (j == 2 ? R.cell[2] : R.cell[3]));
+                    fl[k] = j == 0 ? R.fl[0] : (j == 1 ? R.fl[1] : (j == 2 ? R.fl[2] : R.fl[3]));
+                    sl[k] = f - b;
+                    q[k] = a.cell_pos[(long long)cl[k] * a.cap + sl[k]];
+                }
+            }
 #pragma unroll
-            for (int i = 0; i < kRowItems; ++i) meta[rr * kRowItems + i] = -1;
-            if (r < rows) {
-                const Row R = row(t, r);
-#pragma unroll
-                for (int i = 0; i < kRowItems; ++i) {
-                    const int f = lane + 32 * i;
-                    if (f < R.tot) {
-                        int cell, slot;
-                        uint32_t fl;
-                        locate(R, f, cell, slot, fl);
-                        it[rr * kRowItems + i] = a.cell_pos[(long long)cell * a.cap + slot];
-                        meta[rr * kRowItems + i] = meta_of(t, cell, slot, fl);
+            for (int k = 0; k < 4; ++k) {
+                if (cl[k] == t.co && cl[k] >= 0) {
+                    if (q[k].w == t.Po.w) my_self = sl[k];
+                    else if (sl[k] == (int)cnt[cl[k]] - 1) {
+                        my_last = 1;
+                        my_lv = q[k];
+                    }
+                }
+                if constexpr (P32) {
+                    if (t.type == 0) item32<3>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
+                    else if (t.type == 1) item32<2>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
+                    else item32<1>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
+                } else if (cl[k] >= 0 && q[k].w != t.Po.w) {
+                    const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q[k].w);
+                    if (fl[k] & kOld) pair_terms<false>(t.Po, q[k], a, kk, -1.f, e, ua, de, da);
+                    if (fl[k] & kNew) pair_terms<false>(t.Pn, q[k], a, kk, 1.f, e, ua, de, da);
+                }
+            }
+            // dense rows: items beyond the first 64 of a row
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                const Row &R = k ? R1 : R0;
+                for (int f = 64 + lane; f < R.tot; f += 32) {
+                    const int j = (f >= R.p1) + (f >= R.p2) + (f >= R.p3);
+                    const int b = j == 0 ? 0 : (j == 1 ? R.p1 : (j == 2 ? R.p2 : R.p3));
+                    const int c = j == 0 ? R.cell[0] : (j == 1 ? R.cell[1] : (j == 2 ? R.cell[2] : R.cell[3]));
+                    const uint32_t g = j == 0 ? R.fl[0] : (j == 1 ? R.fl[1] : (j == 2 ? R.fl[2] : R.fl[3]));
+                    const int sl2 = f - b;
+                    const uint4 qq = a.cell_pos[(long long)c * a.cap + sl2];
+                    if (c == t.co) {
+                        if (qq.w == t.Po.w) my_self = sl2;
+                        else if (sl2 == (int)cnt[c] - 1) {
+                            my_last = 1;
+                            my_lv = qq;
+                        }
+                    }
+                    if constexpr (P32) {
+                        if (t.type == 0) item32<3>(t, dp, qq, true, g, acc, mag);
+                        else if (t.type == 1) item32<2>(t, dp, qq, true, g, acc, mag);
+                        else item32<1>(t, dp, qq, true, g, acc, mag);
+                    } else if (qq.w != t.Po.w) {
+                        const int kk = (int)t.s * kMaxSpecies + (int)tag_species(qq.w);
+                        if (g & kOld) pair_terms<false>(t.Po, qq, a, kk, -1.f, e, ua, de, da);
+                        if (g & kNew) pair_terms<false>(t.Pn, qq, a, kk, 1.f, e, ua, de, da);
                     }
                 }
             }
         }
-    }
-
-    // pair sums of one item (recording the trial particle's slot and the old
-    // cell's last particle for the update)
-    template <bool P32>
-    __device__ __forceinline__ void item(const Trial &t, const uint4 &q, int mt, bool record, FF &e, float &ua,
-                                         double &de, double &da) const
-    {
-        if (q.w == t.Po.w) {
-            if (record && (mt & (1 << 18))) sh.self_slot = mt & 0xFFFF;
-            return;
+        if constexpr (P32) {
+            e = FF{warp_sum(acc), 0.f};
+            ua = warp_sum(mag);
+        } else {
+            de = warp_sum(de);
+            da = warp_sum(da);
         }
-        if (record && (mt & (1 << 19))) sh.last_val = q;
-        const int kk = t.c.s * kMaxSpecies + (int)tag_species(q.w);
-        const uint32_t fl = (mt >> 16) & 3;
-        if (fl & kOld) pair_terms<P32>(t.Po, q, a, kk, -1.f, e, ua, de, da);
-        if (fl & kNew) pair_terms<P32>(t.Pn, q, a, kk, 1.f, e, ua, de, da);
+        const unsigned bs = __ballot_sync(0xffffffffu, my_self >= 0);
+        self_slot = bs ? __shfl_sync(0xffffffffu, my_self, __ffs(bs) - 1) : -1;
+        const unsigned bl = __ballot_sync(0xffffffffu, my_last != 0);
+        found_last = bl ? 1 : 0;
+        const int src = bl ? __ffs(bl) - 1 : 0;
+        last_val.x = __shfl_sync(0xffffffffu, my_lv.x, src);
+        last_val.y = __shfl_sync(0xffffffffu, my_lv.y, src);
+        last_val.z = __shfl_sync(0xffffffffu, my_lv.z, src);
+        last_val.w = __shfl_sync(0xffffffffu, my_lv.w, src);
     }
 
-    // every item of the trial: the registers first, the rest (dense cells,
-    // rows beyond the second per warp) straight from memory
-    template <bool P32>
-    __device__ __forceinline__ void sum_items(const Trial &t, const uint4 *it, const int *meta, bool record, FF &e, float &ua,
-                              double &de, double &da) const
+    // the words of moves [m0, m0 + count) (count <= 32), computed by one warp
+    __device__ __forceinline__ void fill_words(int m0, int count) const
     {
-#pragma unroll
-        for (int k = 0; k < kSlots; ++k)
-            if (meta[k] >= 0) item<P32>(t, it[k], meta[k], record, e, ua, de, da);
-        const int rows = nrows(t);
-        for (int r = warp; r < rows; r += kWarpsW) {
-            const Row R = row(t, r);
-            const int f0 = (r < warp + kRowsW * kWarpsW) ? 32 * kRowItems : 0;
-            for (int f = f0 + lane; f < R.tot; f += 32) {
-                int cell, slot;
-                uint32_t fl;
-                locate(R, f, cell, slot, fl);
-                const uint4 q = a.cell_pos[(long long)cell * a.cap + slot];
-                item<P32>(t, q, meta_of(t, cell, slot, fl), record, e, ua, de, da);
-            }
+        const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        if (lane < count) {
+            const uint64_t m = a.first + (uint64_t)(m0 + lane);
+            const uint4 r0 = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, 0u), key);
+            const uint4 r1 = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, 1u), key);
+            WordRec &W = sh.words[(int)(m % kRW)];
+            W.w[0] = r0.x;
+            W.w[1] = r0.y;
+            W.w[2] = r0.z;
+            W.w[3] = r0.w;
+            W.w[4] = r1.x;
+            W.w[5] = r1.y;
+            W.w[6] = r1.z;
+            W.w[7] = r1.w;
+            const uint64_t k53 = ((uint64_t)(r1.z >> 5) << 26) | (uint64_t)(r1.w >> 6);
+            float l;
+            if (k53 == 0) l = -INFINITY;                                   // u = 0: always accept
+            else if (k53 < (1ull << 27)) l = __int_as_float(0x7fc00000);  // u < 2^-26: decide in FP64
+            else l = logf((float)((double)k53 * 1.1102230246251565404e-16));
+            W.lnu = l;
         }
     }
 
-    __device__ __forceinline__ void note_cell(int &nm, int x, int y, int z) const
+    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z) const
     {
-        sh.mod_x[nm] = x;
-        sh.mod_y[nm] = y;
-        sh.mod_z[nm] = z;
+        L.mx[nm] = x;
+        L.my[nm] = y;
+        L.mz[nm] = z;
         ++nm;
     }
 
-    // Warp 0: apply an accepted move (Sec. 3.2.5) and record what it changed.
-    __device__ __forceinline__ void apply(const Trial &t, int &ncell_mod, int &nid) const
+    // Committer: apply an accepted move (Sec. 3.2.5), log what it changed.
+    __device__ __forceinline__ void apply(const Trial &t, int self_slot, const uint4 &last_val, LogRec &L) const
     {
-        const int sp = t.c.s;
+        const int sp = t.s;
         const long long sb = (long long)sp * a.maxN;
-        const int type = t.c.type;
-        if (type != 2) {
+        int nm = 0, nid = 0;
+        if (t.type != 2) {
             if (lane == 0) {
-                if (type == 0) {
+                if (t.type == 0) {
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, t.Po.w);
                     if (!t.cross) {
-                        a.cell_pos[(long long)t.co * a.cap + sh.self_slot] = v;
-                        note_cell(ncell_mod, t.px, t.py, t.pz);
+                        a.cell_pos[(long long)t.co * a.cap + self_slot] = v;
+                        note(L, nm, t.px, t.py, t.pz);
                     } else {
                         const int c_o = cnt[t.co];
-                        if (sh.self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + sh.self_slot] = sh.last_val;
+                        if (self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
                         cnt[t.co] = (uint16_t)(c_o - 1);
                         const int c_n = cnt[t.cn];
                         a.cell_pos[(long long)t.cn * a.cap + c_n] = v;
                         cnt[t.cn] = (uint16_t)(c_n + 1);
-                        note_cell(ncell_mod, t.px, t.py, t.pz);
-                        note_cell(ncell_mod, t.qx, t.qy, t.qz);
+                        note(L, nm, t.px, t.py, t.pz);
+                        note(L, nm, t.qx, t.qy, t.qz);
                     }
-                    a.pos_by_id[sb + t.c.idx] = v;
-                    sh.mod_ids[nid++] = (sp << 24) | t.c.idx;
+                    a.pos_by_id[sb + t.idx] = v;
+                    L.ids[nid++] = (sp << 24) | t.idx;
                 } else {
                     const long long ni = sh.n[sp];
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, make_tag((uint32_t)ni, (uint32_t)sp));
@@ -577,9 +687,12 @@ struct Chain {
                     sh.n[sp] = ni + 1;
                     sh.ln_n[sp] = logf((float)(ni + 1));
                     sh.ln_n1[sp] = logf((float)(ni + 2));
-                    note_cell(ncell_mod, t.qx, t.qy, t.qz);
-                    sh.mod_ids[nid++] = (sp << 24) | (int)ni;
+                    note(L, nm, t.qx, t.qy, t.qz);
+                    L.ids[nid++] = (sp << 24) | (int)ni;
                 }
+                for (int q = nm; q < 3; ++q) L.mx[q] = -1;
+                for (int q = nid; q < 3; ++q) L.ids[q] = -1;
+                L.flags = 1 | ((t.type == 1) ? 2 : 0);
             }
             return;
         }
@@ -588,18 +701,19 @@ struct Chain {
         const long long last = sh.n[sp] - 1;
         if (lane == 0) {
             const int c_o = cnt[t.co];
-            if (sh.self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + sh.self_slot] = sh.last_val;
+            if (self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
             cnt[t.co] = (uint16_t)(c_o - 1);
-            note_cell(ncell_mod, t.px, t.py, t.pz);
-            sh.mod_ids[nid++] = (sp << 24) | t.c.idx;
         }
         __syncwarp();
-        if (t.c.idx != last) {
+        int qx = -1, qy = 0, qz = 0;
+        if (t.idx != last) {
             const uint4 Q = a.pos_by_id[sb + last];
-            const int qx = cell_coord(Q.x, uT), qy = cell_coord(Q.y, uT), qz = cell_coord(Q.z, uT);
+            qx = cell_coord(Q.x, uT);
+            qy = cell_coord(Q.y, uT);
+            qz = cell_coord(Q.z, uT);
             const int cq = (qz * T + qy) * T + qx;
             const int cc = cnt[cq];
-            const uint32_t ntag = make_tag((uint32_t)t.c.idx, (uint32_t)sp);
+            const uint32_t ntag = make_tag((uint32_t)t.idx, (uint32_t)sp);
             for (int base = 0; base < cc; base += 32) {
                 const int j = base + lane;
                 bool hit = false;
@@ -608,13 +722,18 @@ struct Chain {
                 if (hit) a.cell_pos[(long long)cq * a.cap + j].w = ntag;
                 if (hb) break;
             }
-            if (lane == 0) {
-                a.pos_by_id[sb + t.c.idx] = make_uint4(Q.x, Q.y, Q.z, ntag);
-                note_cell(ncell_mod, qx, qy, qz);
-                sh.mod_ids[nid++] = (sp << 24) | (int)last;
-            }
+            if (lane == 0) a.pos_by_id[sb + t.idx] = make_uint4(Q.x, Q.y, Q.z, ntag);
         }
         if (lane == 0) {
+            note(L, nm, t.px, t.py, t.pz);
+            L.ids[nid++] = (sp << 24) | t.idx;
+            if (qx >= 0) {
+                note(L, nm, qx, qy, qz);
+                L.ids[nid++] = (sp << 24) | (int)last;
+            }
+            for (int q = nm; q < 3; ++q) L.mx[q] = -1;
+            for (int q = nid; q < 3; ++q) L.ids[q] = -1;
+            L.flags = 3;
             sh.n[sp] = last;
             sh.ln_n[sp] = logf((float)last);
             sh.ln_n1[sp] = logf((float)(last + 1));
@@ -622,381 +741,485 @@ struct Chain {
     }
 };
 
-// Move record handed from the deciding warp to the bookkeeping warp.
-struct MoveRec {
-    double dU;
-    float tot_hi, tot_lo;  // FP32-path total (float-float)
-    float uab;
-    int fin;      // bit0 accepted, bit1 stop
-    int type, sp, index;
-    int possible;
-    int refined;  // decided in FP64 (bit1 of the trace flag); bit0 = near threshold
-    double lnA;   // FP64 path only
+// Whether a move evaluated after `c0` commits is still valid after `m`: no
+// committed move in [c0, m) touched its cells or wrote its particle's record,
+// and the current particle counts pick the same particle (or, for a move
+// that was impossible, still make it impossible).
+template <bool F32>
+__device__ __forceinline__ bool still_valid(const Chain<F32> &C, const Shared &sh, const Trial &t, int c0, int m,
+                                            int T, int lane)
+{
+    bool bad = false;
+    bool nchanged = false;
+    for (int j = c0 + lane; j < m; j += 32) {
+        const LogRec &L = sh.logs[j % kRS];
+        const int f = L.flags;
+        if (!(f & 1)) continue;
+        if (f & 2) nchanged = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (L.mx[q] >= 0 && in_work(t, L.mx[q], L.my[q], L.mz[q], T)) bad = true;
+            if (t.possible && t.type != 1 && L.ids[q] >= 0 && L.ids[q] == (((int)t.s << 24) | t.idx)) bad = true;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad)) return false;
+    if (t.type != 1 && __any_sync(0xffffffffu, nchanged)) {
+        // N changed: the move stands only if the same particle is chosen
+        const int *ns = sh.ns_ring[m % kRS];
+        const WordRec &W = C.words(m);
+        int s = 0, idx = -1, possible = 1;
+        if (t.type == 0) {
+            int N = 0;
+            for (int q = 0; q < C.a.S; ++q) N += ns[q];
+            if (N == 0) {
+                possible = 0;
+            } else {
+                int k = (int)__umulhi(W.w[1], (uint32_t)N);
+                while (k >= ns[s]) {
+                    k -= ns[s];
+                    ++s;
+                }
+                idx = k;
+            }
+        } else {
+            s = (int)t.s;
+            if (ns[s] == 0) possible = 0;
+            else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
+        }
+        if (possible != (int)t.possible) return false;
+        if (possible && (s != (int)t.s || idx != t.idx)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void team_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Per-team hand-off area: the leader's decision for the team and the
+// warps' partial sums.
+template <int G>
+struct TeamShared {
+    Trial t;  // the trial, computed once by the leader warp
+    int go;   // 1 evaluate move m, 2 finished
+    int m;
+    int c0;
+    int pad;
+    float hi[G], lo[G], ua[G];
+    int self[G];
+    int has_last[G];
+    uint4 last[G];
 };
 
-// NT worker threads (the pair work) plus one bookkeeping warp that keeps
-// the FP64 running energy, the averages, the counters and the trace, and
-// refills the random-word ring -- all off the per-move critical path.
-template <bool F32, int NT>
-__global__ void __launch_bounds__(NT + 32, 1) k_chain(const ChainArgs a)
+// NTEAM teams of G evaluator warps (warps 1 .. G * NTEAM), the committer
+// (warp 0) and the keeper (last warp).  Each team evaluates every
+// NTEAM-th move, its rows spread over the team's warps; a team has at most
+// one uncommitted move, so a move is evaluated at most NTEAM - 1 commits
+// ahead of its turn.
+template <bool F32, int G, int NTEAM>
+__global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const __grid_constant__ ChainArgs a)
 {
+    constexpr int EW = G * NTEAM;
+    constexpr int NTH = (EW + 2) * 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     uint16_t *cnt = (uint16_t *)dyn;
-    __shared__ ChainSmem<NT> sh;
-    __shared__ MoveRec rec;
-    Chain<F32, NT> C(a, sh, cnt);
-    const int tid = C.tid, lane = C.lane, warp = C.warp, T = C.T;
-    const bool worker = tid < NT;
-    const bool keeper = warp == NT / 32;
+    __shared__ Shared sh;
+    __shared__ TeamShared<G> ts[NTEAM];
+    __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
+    Chain<F32> C(a, sh, cnt);
+    const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
+    const int n = a.n_moves;
+    const int keeper_warp = EW + 1;
 
-    for (int c = tid; c < a.ncell; c += NT + 32) cnt[c] = (uint16_t)a.cell_count[c];
+    for (int c = tid; c < a.ncell; c += NTH) cnt[c] = (uint16_t)a.cell_count[c];
     if (tid < kMaxSpecies) {
         const long long v = tid < a.S ? a.d_n[tid] : 0;
         sh.n[tid] = v;
         sh.ln_n[tid] = logf((float)v);
         sh.ln_n1[tid] = logf((float)(v + 1));
+        sh.ns_ring[0][tid] = (int)v;
     }
-    const long long n_moves = a.n_moves;
-    fill_ring<NT>(sh, a, a.first, (int)llmin_(kRefill, n_moves));
-    if (n_moves > kRefill) fill_ring<NT>(sh, a, a.first + kRefill, (int)llmin_(kRefill, n_moves - kRefill));
+    for (int k = tid; k < kRS; k += NTH) {
+        sh.slots[k].ready = 0;
+        sh.book[k].ready = 0;
+        sh.logs[k].flags = 0;
+    }
+    if (tid < NTEAM) redo[tid] = 0;
+    if (tid == 0) {
+        sh.committed = 0;
+        sh.booked = 0;
+        sh.stop = 0;
+        sh.status = 0;
+    }
+    {
+        const int first_fill = min(n, kRW);
+        for (int b = warp; b * kFill < first_fill; b += EW + 2)
+            C.fill_words(b * kFill, min(kFill, first_fill - b * kFill));
+        if (tid == 0) sh.filled = first_fill;
+    }
     __syncthreads();
 
-    // bookkeeping state (keeper lane 0 only), kept in shared memory
-    __shared__ struct {
-        double E, sumE;
-        long long sumN, att[3], acc[3], flagged, done, refines, Ncur;
-        int status;
-    } kp;
-    int refetch = 0;
-    if (keeper && lane == 0) {
-        kp.E = *a.d_energy;
-        kp.sumE = 0.0;
-        kp.sumN = 0;
-        for (int q = 0; q < 3; ++q) kp.att[q] = kp.acc[q] = 0;
-        kp.flagged = kp.done = kp.refines = 0;
-        kp.status = 0;
-        long long N0 = 0;
-        for (int q = 0; q < kMaxSpecies; ++q) N0 += sh.n[q];
-        kp.Ncur = N0;
-    }
-
-    uint4 it_cur[kSlots], it_nxt[kSlots];
-    int meta_cur[kSlots], meta_nxt[kSlots];
-    Trial tr_cur, tr_nxt;
-    Choice ch_nn;
-    uint4 rec_nn = make_uint4(0, 0, 0, 0);
-    if (worker) {
-        const Choice c0 = C.choose(0);
-        tr_cur = C.finish(c0, C.load_rec(c0), 0);
-        C.gather(tr_cur, it_cur, meta_cur);
-        if (n_moves > 1) {
-            const Choice c1 = C.choose(1);
-            tr_nxt = C.finish(c1, C.load_rec(c1), 1);
-        }
-    }
-    bool valid_cur = true, valid_nxt = true;
-    const float beta_f = (float)a.beta, tol_f = (float)a.tol;
-
-    for (long long mm = 0; mm < n_moves; ++mm) {
-        const bool have_nxt = mm + 1 < n_moves;
-        const bool have_nn = mm + 2 < n_moves;
-        if (worker) {
-            // A. the current move, re-fetched when the previous move invalidated it
-            if (!valid_cur) {
-                const Choice c = C.choose(mm);
-                tr_cur = C.finish(c, C.load_rec(c), mm);
-                C.gather(tr_cur, it_cur, meta_cur);
-                ++refetch;
-            }
-            // B. the next move: its trial (re-chosen when invalid) and its items
-            if (have_nxt) {
-                if (!valid_nxt) {
-                    const Choice c = C.choose(mm + 1);
-                    tr_nxt = C.finish(c, C.load_rec(c), mm + 1);
+    if (warp >= 1 && warp <= EW) {
+        // ------------------------------------------------------------ evaluators
+        const int team = (warp - 1) / G, j = (warp - 1) % G;
+        TeamShared<G> &tsh = ts[team];
+        int next = team;  // the team's next new move (leader lane 0)
+        for (;;) {
+            if (j == 0 && lane == 0) {
+                long long spins = 0;
+                for (;;) {
+                    const int com = vload(sh.committed);
+                    if (vload(sh.stop)) {
+                        tsh.go = 2;
+                        break;
+                    }
+                    const int rd = vload(redo[team]);
+                    if (rd) {
+                        vstore(redo[team], 0);
+                        tsh.m = rd - 1;
+                        tsh.c0 = com;
+                        tsh.go = 1;
+                        break;
+                    }
+                    if (next < n && next <= com + NTEAM && next < vload(sh.filled)) {
+                        tsh.m = next;
+                        tsh.c0 = com;
+                        tsh.go = 1;
+                        next += NTEAM;
+                        break;
+                    }
+                    if (next >= n && com >= n) {
+                        tsh.go = 2;
+                        break;
+                    }
+                    if (++spins > kSpinMax) {
+                        atomicOr(&sh.status, kStatusTimeout);
+                        vstore(sh.stop, 1);
+                        tsh.go = 2;
+                        break;
+                    }
+                    __nanosleep(16);
                 }
-                C.gather(tr_nxt, it_nxt, meta_nxt);
+                __threadfence_block();
             }
-            // C. the record of move mm + 2
-            if (have_nn) {
-                ch_nn = C.choose(mm + 2);
-                rec_nn = C.load_rec(ch_nn);
+            if (j == 0) {
+                __syncwarp();
+                if (tsh.go == 1) {
+                    const Trial tt = C.make_trial(tsh.m, sh.ns_ring[tsh.c0 % kRS]);
+                    if (lane == 0) tsh.t = tt;
+                }
             }
-            // D. pair sums of the current move
-            FF e = {0.f, 0.f};
-            float ua = 0.f;
-            double de = 0.0, da = 0.0;
-            C.template sum_items<F32>(tr_cur, it_cur, meta_cur, true, e, ua, de, da);
+            team_sync(1 + team, G * 32);
+            const int go = tsh.go, m = tsh.m, c0 = tsh.c0;
+            if (go == 2) break;
+            const Trial t = tsh.t;
+            FF e;
+            float ua;
+            double de, da;
+            int self_slot, found_last;
+            uint4 last_val;
+            C.template energy<F32>(t, j, G, e, ua, de, da, self_slot, last_val, found_last);
             if constexpr (!F32) {
-                const float h = __double2float_rn(de);
-                e.hi = h;
-                e.lo = __double2float_rn(de - (double)h);
+                e.hi = __double2float_rn(de);
+                e.lo = __double2float_rn(de - (double)e.hi);
                 ua = (float)da;
             }
-            e = ff_warp_sum(e);
-            ua = warp_sum(ua);
             if (lane == 0) {
-                sh.red_hi[warp] = e.hi;
-                sh.red_lo[warp] = e.lo;
-                sh.red_a[warp] = ua;
+                tsh.hi[j] = e.hi;
+                tsh.lo[j] = e.lo;
+                tsh.ua[j] = ua;
+                tsh.self[j] = self_slot;
+                tsh.has_last[j] = found_last;
+                tsh.last[j] = last_val;
+            }
+            team_sync(1 + team, G * 32);
+            if (j == 0) {
+                FF tot = {0.f, 0.f};
+                float uab = 0.f;
+                int self = -1, hl = 0;
+                uint4 lv = make_uint4(0, 0, 0, 0);
+                if (lane < G) {
+                    tot.hi = tsh.hi[lane];
+                    tot.lo = tsh.lo[lane];
+                    uab = tsh.ua[lane];
+                    self = tsh.self[lane];
+                    hl = tsh.has_last[lane];
+                    lv = tsh.last[lane];
+                }
+                tot = ff_warp_sum(tot);
+                uab = warp_sum(uab);
+                const unsigned bs = __ballot_sync(0xffffffffu, self >= 0);
+                const unsigned bl = __ballot_sync(0xffffffffu, hl != 0);
+                const int src_s = bs ? __ffs(bs) - 1 : 0, src_l = bl ? __ffs(bl) - 1 : 0;
+                const int self_all = bs ? __shfl_sync(0xffffffffu, self, src_s) : -1;
+                uint4 lv_all;
+                lv_all.x = __shfl_sync(0xffffffffu, lv.x, src_l);
+                lv_all.y = __shfl_sync(0xffffffffu, lv.y, src_l);
+                lv_all.z = __shfl_sync(0xffffffffu, lv.z, src_l);
+                lv_all.w = __shfl_sync(0xffffffffu, lv.w, src_l);
+                if (lane == 0) {
+                    Slot &S = sh.slots[m % kRS];
+                    S.t = t;
+                    S.last_val = lv_all;
+                    S.hi = tot.hi;
+                    S.lo = tot.lo;
+                    S.uab = uab;
+                    S.self_slot = self_all;
+                    S.c0 = c0;
+                    __threadfence_block();
+                    vstore(S.ready, m + 1);
+                }
+                __syncwarp();
             }
         }
-        __syncthreads();  // B1
-        const Trial &t = tr_cur;
-        const int sp = t.c.s;
-        // E. warp 0 decides in FP32 with an error band and applies
-        if (warp == 0) {
-            FF tot = {0.f, 0.f};
-            float uab = 0.f;
-            if (lane < NT / 32) {
-                tot.hi = sh.red_hi[lane];
-                tot.lo = sh.red_lo[lane];
-                uab = sh.red_a[lane];
+    } else if (warp == 0) {
+        // ------------------------------------------------------------ committer
+        const float beta_f = (float)a.beta, tol_f = (float)a.tol;
+        for (int m = 0; m < n; ++m) {
+            Slot &S = sh.slots[m % kRS];
+            const int team = m % NTEAM;
+            bool ok = true;
+            int c0 = 0, attempt = 0;
+            for (;; ++attempt) {
+                // wait for the evaluation of m and for room in the keeper's book
+                long long spins = 0;
+                for (;;) {
+                    int r = 0, bk = 0;
+                    if (lane == 0) {
+                        r = vload(S.ready);
+                        bk = vload(sh.booked);
+                    }
+                    r = __shfl_sync(0xffffffffu, r, 0);
+                    bk = __shfl_sync(0xffffffffu, bk, 0);
+                    if (r == m + 1 && m < bk + kRS) break;
+                    if (++spins > kSpinMax) {
+                        if (lane == 0) atomicOr(&sh.status, kStatusTimeout);
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) break;
+                __threadfence_block();
+                c0 = S.c0;
+                if (c0 == m || still_valid<F32>(C, sh, S.t, c0, m, T, lane)) break;
+                // evaluate again against the configuration after m moves
+                if (lane == 0) {
+                    vstore(S.ready, 0);
+                    __threadfence_block();
+                    vstore(redo[team], m + 1);
+                }
+                __syncwarp();
             }
-#pragma unroll
-            for (int o = (NT / 64); o > 0; o >>= 1) {
-                FF w2;
-                w2.hi = __shfl_xor_sync(0xffffffffu, tot.hi, o);
-                w2.lo = __shfl_xor_sync(0xffffffffu, tot.lo, o);
-                tot = ff_add(tot, w2);
-                uab += __shfl_xor_sync(0xffffffffu, uab, o);
-            }
-            tot.hi = __shfl_sync(0xffffffffu, tot.hi, 0);
-            tot.lo = __shfl_sync(0xffffffffu, tot.lo, 0);
-            uab = __shfl_sync(0xffffffffu, uab, 0);
-            const int type = t.c.type;
-            int dec = 0;
-            if (t.c.possible) {
-                const float lnu = sh.lnu[(int)((a.first + (uint64_t)mm) % kRing)];
+            if (!ok) break;
+            const Trial t = S.t;
+            FF e = {S.hi, S.lo};
+            float uab = S.uab;
+            const int self_slot = S.self_slot;
+            const uint4 last_val = S.last_val;
+            int refined = attempt > 0 ? 4 : 0;
+            const int type = t.type, sp = t.s;
+            const long long ns = sh.n[sp];
+            // Metropolis test in FP32 with an error band
+            int fin = 0;
+            double dU = (double)e.hi + (double)e.lo, lnA_d = 0.0;
+            bool decided = true;
+            if (t.possible) {
+                const float lnu = C.words(m).lnu;
                 float lnK = 0.f;
                 if (type == 1) lnK = a.lnzv_f[sp] - sh.ln_n1[sp];
                 else if (type == 2) lnK = sh.ln_n[sp] - a.lnzv_f[sp];
-                const float dUf = tot.hi + tot.lo;
+                const float dUf = e.hi + e.lo;
                 const float lnA = lnK - beta_f * dUf;
                 const float band =
                     beta_f * tol_f * uab + 1e-6f * (1.f + fabsf(lnK) + fabsf(beta_f * dUf) + fabsf(lnu));
                 const float diff = lnu - lnA;
-                if (!(fabsf(diff) > band)) dec = 4;  // near the threshold, or not finite
-                else dec = (diff < 0.f) ? 1 : 0;
+                if (fabsf(diff) > band) fin = (diff < 0.f) ? 1 : 0;
+                else decided = false;  // near the threshold, or not finite
             }
-            if (!(dec & 4)) {
-                int fin = dec;
-                if (dec & 1) {
-                    if (type == 1 && sh.n[sp] >= a.maxN) fin = 2 | 8;
-                    else if ((type == 1 || t.cross) && cnt[t.cn] >= a.cap) fin = 2 | 16;
-                }
-                int ncm = 0, nid = 0;
-                if (lane == 0) {
-                    rec.type = type;
-                    rec.sp = sp;
-                    rec.index = (type == 1 && t.c.possible) ? (int)sh.n[sp] : t.c.idx;
-                    rec.possible = t.c.possible;
-                    rec.dU = 0.0;  // filled by the keeper from hi/lo
-                    rec.uab = uab;
-                    rec.refined = 0;
-                    rec.tot_hi = tot.hi;
-                    rec.tot_lo = tot.lo;
-                }
-                if (!(fin & 2) && (fin & 1)) C.apply(t, ncm, nid);
-                if (lane == 0) {
-                    rec.fin = fin;
-                    for (int q = ncm; q < 3; ++q) sh.mod_x[q] = -1;
-                    for (int q = nid; q < 3; ++q) sh.mod_ids[q] = -1;
-                    sh.nchanged = ((fin & 1) && !(fin & 2) && type != 0) ? 1 : 0;
-                    sh.decision = fin & 3;
-                }
-            } else if (lane == 0) {
-                sh.decision = 4;
-            }
-        }
-        __syncthreads();  // B2
-        int dec = sh.decision;
-        if (dec & 4) {
-            // ---- the whole trial again in FP64 (pair terms, sums, log)
-            if (worker) {
-                FF ed = {0.f, 0.f};
-                float ud = 0.f;
-                double rd = 0.0, ra = 0.0;
-                C.template sum_items<false>(t, it_cur, meta_cur, false, ed, ud, rd, ra);
-                rd = warp_sum(rd);
-                ra = warp_sum(ra);
-                if (lane == 0) {
-                    sh.red_d[warp] = rd;
-                    sh.red_da[warp] = ra;
-                }
-            }
-            __syncthreads();
-            if (warp == 0) {
-                double dU = 0.0, uab = 0.0;
-                for (int q = 0; q < NT / 32; ++q) {
-                    dU += sh.red_d[q];
-                    uab += sh.red_da[q];
-                }
-                const int type = t.c.type;
-                const uint32_t *w = C.words(mm);
-                const double lnu = log(uniform53(w[6], w[7]));
+            if (!decided) {
+                // the whole trial in FP64: pair terms, sums, log
+                FF e2;
+                float u2;
+                double de, da;
+                int s2, f2;
+                uint4 l2;
+                C.template energy<false>(t, 0, 1, e2, u2, de, da, s2, l2, f2);
+                const WordRec &W = C.words(m);
+                const double lnu = log(uniform53(W.w[6], W.w[7]));
                 double lnK = 0.0;
-                if (type == 1) lnK = a.logz[sp] + a.lnV - log((double)(sh.n[sp] + 1));
-                else if (type == 2) lnK = log((double)sh.n[sp]) - a.logz[sp] - a.lnV;
-                const double lnA = lnK - a.beta * dU;
-                int fin = (lnu < lnA) ? 1 : 0;
-                const double band = a.beta * a.tol * uab + 1e-12 * (1.0 + fabs(lnA));
-                const int flag = (fabs(lnu - lnA) <= band) ? 1 : 0;
-                if (fin & 1) {
-                    if (type == 1 && sh.n[sp] >= a.maxN) fin = 2 | 8;
-                    else if ((type == 1 || t.cross) && cnt[t.cn] >= a.cap) fin = 2 | 16;
-                }
-                int ncm = 0, nid = 0;
-                if (lane == 0) {
-                    rec.type = type;
-                    rec.sp = sp;
-                    rec.index = (type == 1) ? (int)sh.n[sp] : t.c.idx;
-                    rec.possible = 1;
-                    rec.dU = dU;
-                    rec.uab = (float)uab;
-                    rec.lnA = lnA;
-                    rec.refined = 2 | flag;
-                }
-                if (!(fin & 2) && (fin & 1)) C.apply(t, ncm, nid);
-                if (lane == 0) {
-                    rec.fin = fin;
-                    for (int q = ncm; q < 3; ++q) sh.mod_x[q] = -1;
-                    for (int q = nid; q < 3; ++q) sh.mod_ids[q] = -1;
-                    sh.nchanged = ((fin & 1) && !(fin & 2) && type != 0) ? 1 : 0;
-                    sh.decision = fin & 3;
-                }
+                if (type == 1) lnK = a.logz[sp] + a.lnV - log((double)(ns + 1));
+                else if (type == 2) lnK = log((double)ns) - a.logz[sp] - a.lnV;
+                lnA_d = lnK - a.beta * de;
+                fin = (lnu < lnA_d) ? 1 : 0;
+                const double band = a.beta * a.tol * da + 1e-12 * (1.0 + fabs(lnA_d));
+                refined |= 2 | ((fabs(lnu - lnA_d) <= band) ? 1 : 0);
+                dU = de;
+                uab = (float)da;
             }
-            __syncthreads();
-            dec = sh.decision;
-        }
-        // F. the keeper: FP64 running energy, averages, counters, trace; ring refill
-        if (keeper) {
+            int stop_bits = 0;
+            if (fin & 1) {
+                if (type == 1 && ns >= a.maxN) stop_bits = kStatusCapacity;
+                else if ((type == 1 || t.cross) && cnt[t.cn] >= a.cap) stop_bits = kStatusCellOverflow;
+            }
+            if (stop_bits) {
+                if (lane == 0) {
+                    atomicOr(&sh.status, stop_bits);
+                    vstore(sh.stop, 1);
+                }
+                break;
+            }
+            LogRec &L = sh.logs[m % kRS];
+            if (fin & 1) C.apply(t, self_slot, last_val, L);
+            else if (lane == 0) L.flags = 0;
+            __syncwarp();
+            if (lane < kMaxSpecies) sh.ns_ring[(m + 1) % kRS][lane] = (int)sh.n[lane];
+            __syncwarp();
             if (lane == 0) {
-                const int fin = rec.fin;
-                if (fin & 8) kp.status |= kStatusCapacity;
-                if (fin & 16) kp.status |= kStatusCellOverflow;
-                if (!(fin & 2)) {
-                    const int type = rec.type;
-                    const double dU = (rec.refined & 2) ? rec.dU : (double)rec.tot_hi + (double)rec.tot_lo;
-                    kp.att[type] += 1;
-                    if (rec.refined & 2) kp.refines += 1;
-                    if (rec.refined & 1) kp.flagged += 1;
-                    if (fin & 1) {
-                        kp.acc[type] += 1;
-                        kp.E += dU;
-                        if (type == 1) kp.Ncur += 1;
-                        if (type == 2) kp.Ncur -= 1;
+                BookRec &B = sh.book[m % kRS];
+                B.dU = dU;
+                B.lnA = lnA_d;
+                B.uab = uab;
+                B.fin = fin;
+                B.type = type;
+                B.sp = sp;
+                B.index = (type == 1) ? (int)ns : t.idx;
+                B.possible = t.possible;
+                B.refined = refined;
+                B.ns = ns;
+                __threadfence_block();
+                vstore(B.ready, m + 1);
+                vstore(sh.committed, m + 1);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) vstore(sh.stop, 1);  // evaluators and keeper wind down
+    } else if (warp == keeper_warp) {
+        // ------------------------------------------------------------ keeper
+        double E = *a.d_energy, sumE = 0.0;
+        long long sumN = 0, att0 = 0, att1 = 0, att2 = 0, acc0 = 0, acc1 = 0, acc2 = 0;
+        long long flagged = 0, reeval = 0, refines = 0, Ncur = 0;
+        for (int q = 0; q < kMaxSpecies; ++q) Ncur += sh.n[q];
+        int mb = 0;
+        long long spins = 0;
+        for (;;) {
+            // refill the words ring ahead of the evaluators
+            int c = 0, f = 0, sp0 = 0;
+            if (lane == 0) {
+                c = vload(sh.committed);
+                f = vload(sh.filled);
+                sp0 = vload(sh.stop);
+            }
+            c = __shfl_sync(0xffffffffu, c, 0);
+            f = __shfl_sync(0xffffffffu, f, 0);
+            sp0 = __shfl_sync(0xffffffffu, sp0, 0);
+            if (f < n && f + kFill <= c + kRW - kFill && !sp0) {
+                const int cntw = min(kFill, n - f);
+                C.fill_words(f, cntw);
+                __threadfence_block();
+                if (lane == 0) vstore(sh.filled, f + cntw);
+                __syncwarp();
+                continue;
+            }
+            // book the committed moves in order
+            int rdy = 0;
+            if (lane == 0 && mb < n) rdy = vload(sh.book[mb % kRS].ready);
+            rdy = __shfl_sync(0xffffffffu, rdy, 0);
+            if (mb < n && rdy == mb + 1) {
+                __threadfence_block();
+                if (lane == 0) {
+                    const BookRec &B = sh.book[mb % kRS];
+                    const int type = B.type;
+                    att0 += type == 0;
+                    att1 += type == 1;
+                    att2 += type == 2;
+                    if (B.refined & 1) ++flagged;
+                    if (B.refined & 2) ++refines;
+                    if (B.refined & 4) ++reeval;
+                    if (B.fin & 1) {
+                        acc0 += type == 0;
+                        acc1 += type == 1;
+                        acc2 += type == 2;
+                        E += B.dU;
+                        Ncur += (type == 1) - (type == 2);
                     }
                     if (a.trace) {
                         gcmc_trace tr;
-                        double lnA = rec.lnA;
-                        if (!(rec.refined & 2)) {
+                        double lnA = B.lnA;
+                        if (!(B.refined & 2)) {
                             double lnK = 0.0;
-                            // N before this move
-                            const long long ns = sh.n[rec.sp] - ((fin & 1) ? (type == 1 ? 1 : (type == 2 ? -1 : 0)) : 0);
-                            if (type == 1) lnK = a.logz[rec.sp] + a.lnV - log((double)(ns + 1));
-                            else if (type == 2 && ns > 0) lnK = log((double)ns) - a.logz[rec.sp] - a.lnV;
-                            lnA = rec.possible ? lnK - a.beta * dU : -INFINITY;
+                            if (type == 1) lnK = a.logz[B.sp] + a.lnV - log((double)(B.ns + 1));
+                            else if (type == 2 && B.ns > 0) lnK = log((double)B.ns) - a.logz[B.sp] - a.lnV;
+                            lnA = B.possible ? lnK - a.beta * B.dU : -INFINITY;
                         }
-                        tr.dU = rec.possible ? dU : 0.0;
+                        tr.dU = B.possible ? B.dU : 0.0;
                         tr.lnA = lnA;
-                        tr.uabs = rec.possible ? (double)rec.uab : 0.0;
-                        tr.index = rec.index;
+                        tr.uabs = B.possible ? (double)B.uab : 0.0;
+                        tr.index = B.index;
                         tr.type = (uint8_t)type;
-                        tr.species = (uint8_t)rec.sp;
-                        tr.accepted = (uint8_t)(fin & 1);
-                        tr.flagged = (uint8_t)rec.refined;
-                        a.trace[mm] = tr;
+                        tr.species = (uint8_t)B.sp;
+                        tr.accepted = (uint8_t)(B.fin & 1);
+                        tr.flagged = (uint8_t)(B.refined & 3);
+                        a.trace[mb] = tr;
                     }
-                    kp.sumE += kp.E;
-                    kp.sumN += kp.Ncur;
-                    kp.done = mm + 1;
+                    sumE += E;
+                    sumN += Ncur;
+                    vstore(sh.booked, mb + 1);
                 }
+                __syncwarp();
+                ++mb;
+                spins = 0;
+                continue;
             }
-            // refill the word ring one move ahead of its use: move mm + 63
-            // reuses the slot of move mm - 1, which nothing reads any more
-            if (mm >= 1 && mm + 63 < n_moves && lane < 2) {
-                const uint64_t m = a.first + (uint64_t)(mm + 63);
-                const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-                const uint4 r = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, (uint32_t)lane), key);
-                const int slot = (int)(m % kRing);
-                sh.w[slot][4 * lane + 0] = r.x;
-                sh.w[slot][4 * lane + 1] = r.y;
-                sh.w[slot][4 * lane + 2] = r.z;
-                sh.w[slot][4 * lane + 3] = r.w;
-                if (lane == 1) {
-                    const uint64_t k53 = ((uint64_t)(r.z >> 5) << 26) | (uint64_t)(r.w >> 6);
-                    float l;
-                    if (k53 == 0) l = -INFINITY;
-                    else if (k53 < (1ull << 27)) l = __int_as_float(0x7fc00000);
-                    else l = logf((float)((double)k53 * 1.1102230246251565404e-16));
-                    sh.lnu[slot] = l;
+            if (mb >= n) break;
+            int stop = 0, com = 0;
+            if (lane == 0) {
+                stop = vload(sh.stop);
+                com = vload(sh.committed);
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            com = __shfl_sync(0xffffffffu, com, 0);
+            if (stop && mb >= com) break;
+            if (++spins > kSpinMax) {
+                if (lane == 0) {
+                    atomicOr(&sh.status, kStatusTimeout);
+                    vstore(sh.stop, 1);
                 }
+                break;
             }
+            __nanosleep(20);
         }
-        if (dec & 2) break;
-        if (worker) {
-            // G. validity of the prefetched next move and of the record of mm + 2
-            bool ok_nxt = true, ok_rec = true;
-            if (dec & 1) {
-                const bool nch = sh.nchanged != 0;
-                if (have_nxt) {
-                    const Trial &x = tr_nxt;
-                    if (nch && x.c.type != 1) ok_nxt = false;
-                    for (int q = 0; q < 3; ++q)
-                        if (sh.mod_x[q] >= 0 && in_work(x, sh.mod_x[q], sh.mod_y[q], sh.mod_z[q], T)) ok_nxt = false;
-                    for (int q = 0; q < 3; ++q) {
-                        const int id = sh.mod_ids[q];
-                        if (id >= 0 && Chain<F32, NT>::needs_rec(x.c) && id == ((x.c.s << 24) | x.c.idx)) ok_nxt = false;
-                    }
-                }
-                if (have_nn) {
-                    if (nch && ch_nn.type != 1) ok_rec = false;
-                    for (int q = 0; q < 3; ++q) {
-                        const int id = sh.mod_ids[q];
-                        if (id >= 0 && Chain<F32, NT>::needs_rec(ch_nn) && id == ((ch_nn.s << 24) | ch_nn.idx))
-                            ok_rec = false;
-                    }
-                }
-            }
-            // H. rotate: next -> current, mm + 2 -> next
-            if (have_nxt) {
-                tr_cur = tr_nxt;
-#pragma unroll
-                for (int k = 0; k < kSlots; ++k) {
-                    it_cur[k] = it_nxt[k];
-                    meta_cur[k] = meta_nxt[k];
-                }
-            }
-            valid_cur = ok_nxt;
-            if (have_nn && ok_rec) tr_nxt = C.finish(ch_nn, rec_nn, mm + 2);
-            valid_nxt = ok_rec;
+        if (lane == 0) {
+            ChainOut &o = *a.out;
+            o.attempted[0] = att0;
+            o.attempted[1] = att1;
+            o.attempted[2] = att2;
+            o.accepted[0] = acc0;
+            o.accepted[1] = acc1;
+            o.accepted[2] = acc2;
+            o.flagged = flagged;
+            o.moves_done = mb;
+            o.energy = E;
+            o.sum_energy = sumE;
+            o.sum_n = (double)sumN;
+            o.reevaluated = reeval;
+            o.refines = refines;
+            *a.d_energy = E;
         }
     }
     __syncthreads();
-    for (int c = tid; c < a.ncell; c += NT + 32) a.cell_count[c] = cnt[c];
+    for (int c = tid; c < a.ncell; c += NTH) a.cell_count[c] = cnt[c];
     if (tid < a.S) a.d_n[tid] = sh.n[tid];
-    if (tid == 0) atomicAdd(&a.out->refetch, refetch);
-    if (keeper && lane == 0) {
-        if (!(kp.E - kp.E == 0.0)) kp.status |= kStatusNonFinite;
-        *a.d_energy = kp.E;
+    if (tid == 0) {
         ChainOut &o = *a.out;
-        for (int q = 0; q < 3; ++q) {
-            o.attempted[q] = kp.att[q];
-            o.accepted[q] = kp.acc[q];
-        }
-        o.flagged = kp.flagged;
-        o.moves_done = kp.done;
-        o.energy = kp.E;
-        o.sum_energy = kp.sumE;
-        o.sum_n = (double)kp.sumN;
         for (int q = 0; q < kMaxSpecies; ++q) o.n[q] = sh.n[q];
-        o.status = kp.status;
-        o.refines = kp.refines;
+        int st = sh.status;
+        if (!(o.energy - o.energy == 0.0)) st |= kStatusNonFinite;
+        o.status = st;
     }
 }
 
-constexpr int kChainThreads = 256;
-static_assert(kChainThreads / 32 == kWarpsW, "worker warps");
+constexpr int kTeamWarps = 7, kTeams = 2;
 
 gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves, const gcmc_move_mix *mix,
                       gcmc_move_stats *stats, gcmc_trace *trace)
@@ -1012,18 +1235,19 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
     if (st != GCMC_OK) return st;
     ChainOut *d_out = (ChainOut *)ctx->d_red;
     const size_t smem = ((size_t)ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16;
-    if (smem + sizeof(ChainSmem<kChainThreads>) + 1024 > ctx->smem_optin)
+    if (smem + sizeof(Shared) + 1024 > ctx->smem_optin)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: too many cells for the on-chip cell counters");
+    if (ctx->T > 1023) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: more than 1023 cells per side");
     int64_t done_total = 0;
     gcmc_status result = GCMC_OK;
     ctx->last_refetch = 0;
     ctx->last_refines = 0;
-    for (int attempt = 0; attempt < 64 && done_total < n_moves; ++attempt) {
+    for (int attempt = 0; attempt < (1 << 20) && done_total < n_moves; ++attempt) {
         ChainArgs a;
         memset(&a, 0, sizeof(a));
         a.seed = seed;
         a.first = first + (uint64_t)done_total;
-        a.n_moves = n_moves - done_total;
+        a.n_moves = (int)std::min<int64_t>(n_moves - done_total, 1 << 30);
         a.chain = 0;
         a.T = ctx->T;
         a.ncell = (int)ctx->ncell;
@@ -1032,6 +1256,14 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
         a.S = ctx->S;
         a.R2 = ctx->R2;
         a.rcg = ctx->rcg;
+        {
+            // FP32 r^2 from exact integer separations carries a relative
+            // error below 1e-6 (1 + D / rc); outside this band the FP32 test
+            // agrees with the exact one
+            const double band = 1e-5 * (1.0 + (double)(int64_t)(mix->max_disp * ctx->q) / (double)ctx->rcg);
+            a.r2lo = (float)((double)ctx->R2 * (1.0 - band));
+            a.r2hi = (float)((double)ctx->R2 * (1.0 + band));
+        }
         a.thr_disp = (unsigned long long)(mix->p_disp * 4294967296.0);
         a.thr_ins = (unsigned long long)((mix->p_disp + mix->p_ins) * 4294967296.0);
         const int64_t D = (int64_t)(mix->max_disp * ctx->q);
@@ -1052,10 +1284,10 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
         a.trace = trace ? trace + done_total : nullptr;
         a.out = d_out;
         const bool f32 = ctx->precision == GCMC_FP32;
-        auto kern = f32 ? k_chain<true, kChainThreads> : k_chain<false, kChainThreads>;
+        auto kern = f32 ? k_chain<true, kTeamWarps, kTeams> : k_chain<false, kTeamWarps, kTeams>;
         GCMC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         GCMC_CUDA(ctx, cudaMemsetAsync(d_out, 0, sizeof(ChainOut), ctx->stream));
-        kern<<<1, kChainThreads + 32, smem, ctx->stream>>>(a);
+        kern<<<1, (kTeamWarps * kTeams + 2) * 32, smem, ctx->stream>>>(a);
         ctx->launches += 1;
         GCMC_CUDA(ctx, cudaGetLastError());
         ChainOut o;
@@ -1077,10 +1309,14 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
         ctx->energy = o.energy;
         ctx->compact_valid = false;
         ctx->order_valid = false;
-        ctx->last_refetch += o.refetch;
+        ctx->last_refetch += o.reevaluated;
         ctx->last_refines += o.refines;
         done_total += o.moves_done;
         if (o.status & kStatusNonFinite) result = GCMC_ERR_NONFINITE;
+        if (o.status & kStatusTimeout) {
+            result = fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_run_moves: a bounded wait inside the chain kernel gave up");
+            break;
+        }
         if (o.status & (kStatusCellOverflow | kStatusCapacity)) {
             const bool grow_cap = (o.status & kStatusCellOverflow) && ctx->cap_req == 0;
             const bool grow_n = (o.status & kStatusCapacity) && ctx->max_particles_req == 0;
@@ -1101,7 +1337,10 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
             }
             continue;
         }
-        break;
+        if (o.moves_done == 0 && a.n_moves > 0) {
+            result = fail(ctx, GCMC_ERR_CUDA, "gcmc_run_moves: the chain kernel made no progress");
+            break;
+        }
     }
     if (stats) *stats = agg;
     return result;

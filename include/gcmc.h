@@ -220,8 +220,51 @@ gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out);
  * Errors: INVALID_ARG. */
 gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined);
 
+/* Team shape of the chain kernel (how its warps split the evaluation of
+ * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape on
+ * the first moves of the next gcmc_run_moves and keep the fastest.  Every
+ * shape takes the same moves and decisions and reaches the same
+ * configuration; in FP32 mode the pair terms are summed in a shape-dependent
+ * order, so dU (and the running energy) may differ in the last bits.
+ * Errors: INVALID_ARG. */
+#define GCMC_CHAIN_CONFIGS 4
+gcmc_status gcmc_set_chain_config(gcmc_ctx *ctx, int32_t config);
+gcmc_status gcmc_get_chain_config(gcmc_ctx *ctx, int32_t *config);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char *gcmc_last_error(gcmc_ctx *ctx);
+
+/* ---- Batches of independent chains (the points of an isotherm) ----------
+ * A batch runs the chains of several built contexts (same device, same
+ * precision) in one launch, one CTA per chain, captured as a CUDA graph on
+ * the batch's own stream and replayed for later rounds.  Chain k draws
+ * Philox counters (m_lo, m_hi, k, 0|1) with its own seed.  The batch keeps
+ * pointers to the contexts; they must outlive it. */
+typedef struct gcmc_batch gcmc_batch;
+
+/* Errors: INVALID_ARG (NULL or repeated contexts, mixed precision or
+ * device), CUDA. */
+gcmc_status gcmc_batch_create(gcmc_ctx *const *ctxs, int32_t n_chains, gcmc_batch **out);
+gcmc_status gcmc_batch_destroy(gcmc_batch *batch);
+
+/* Moves first_move .. first_move + n_moves - 1 of every chain, as
+ * gcmc_run_moves would run them one context at a time.  seeds, mixes:
+ * host, n_chains each; stats: host, n_chains, or NULL.  On the first call
+ * with the automatic team shape, the first moves are timed under every
+ * shape and the fastest is kept.  Errors: as gcmc_run_moves, the first
+ * failing chain's status (its context has the message); INVALID_ARG. */
+gcmc_status gcmc_batch_run_moves(gcmc_batch *batch, const uint64_t *seeds, uint64_t first_move, int64_t n_moves,
+                                 const gcmc_move_mix *mixes, gcmc_move_stats *stats);
+
+/* Sets the team shape (-1 automatic, -2 leave unchanged) and reports the
+ * current one and the per-shape probe times in ms of the last tuning (host,
+ * GCMC_CHAIN_CONFIGS doubles, or NULL).  Errors: INVALID_ARG. */
+gcmc_status gcmc_batch_config(gcmc_batch *batch, int32_t set_config, int32_t *config_out, double *probe_ms);
+
+/* Chain-kernel launches (graph replays included) made by the batch. */
+gcmc_status gcmc_batch_launches(gcmc_batch *batch, int64_t *out);
+
+const char *gcmc_batch_last_error(gcmc_batch *batch);
 
 /* Library version string. */
 const char *gcmc_version(void);

@@ -45,6 +45,7 @@ class Geometry(C.Structure):
 
 
 TRACE_BYTES = 32
+CHAIN_CONFIGS = 4
 
 
 class ProbeResult(C.Structure):
@@ -69,6 +70,14 @@ SIGNATURES = {
     "gcmc_get_geometry": (C.c_int, [_vp, C.POINTER(Geometry)]),
     "gcmc_kernel_launches": (C.c_int, [_vp, _vp]),
     "gcmc_chain_counters": (C.c_int, [_vp, _vp, _vp]),
+    "gcmc_set_chain_config": (C.c_int, [_vp, C.c_int32]),
+    "gcmc_get_chain_config": (C.c_int, [_vp, _vp]),
+    "gcmc_batch_create": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
+    "gcmc_batch_destroy": (C.c_int, [_vp]),
+    "gcmc_batch_run_moves": (C.c_int, [_vp, _vp, C.c_uint64, C.c_int64, _vp, _vp]),
+    "gcmc_batch_config": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    "gcmc_batch_launches": (C.c_int, [_vp, _vp]),
+    "gcmc_batch_last_error": (C.c_char_p, [_vp]),
     "gcmc_last_error": (C.c_char_p, [_vp]),
     "gcmc_version": (C.c_char_p, []),
     "gcmc_probe_latency": (C.c_int, [_vp, C.c_int64, C.POINTER(ProbeResult)]),

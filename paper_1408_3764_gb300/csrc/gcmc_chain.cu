@@ -33,6 +33,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "gcmc_ctx.h"
 
@@ -463,7 +465,7 @@ struct Chain {
     // is decided on the FP32 squared distance except inside a thin band
     // around rc^2, where the exact integer squared distance decides.
     template <int SIDES>
-    __device__ __forceinline__ void item32(const Trial &t, const float3 &dp, const uint4 &q, bool valid, uint32_t fl,
+    __device__ __forceinline__ void item32(const Trial &t, const uint4 &q, bool valid, uint32_t fl,
                                            float &acc, float &mag) const
     {
         const bool use = valid && (q.w != t.Po.w);
@@ -479,12 +481,15 @@ struct Chain {
             int ex = dx, ey = dy, ez = dz;
             float gx = fx, gy = fy, gz = fz;
             if (SIDES == 3 && side == 1) {
+                // the new separation is converted from its exact integer
+                // value: old separation + displacement in FP32 would round
+                // the (possibly long) old separation first
                 ex = (int)(t.Pn.x - q.x);
                 ey = (int)(t.Pn.y - q.y);
                 ez = (int)(t.Pn.z - q.z);
-                gx = fx + dp.x;
-                gy = fy + dp.y;
-                gz = fz + dp.z;
+                gx = (float)ex;
+                gy = (float)ey;
+                gz = (float)ez;
             }
             const uint32_t need = (SIDES == 3) ? (side ? kNew : kOld) : (SIDES == 2 ? kNew : kOld);
             const float r2f = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
@@ -519,9 +524,6 @@ struct Chain {
         ua = 0.f;
         de = da = 0.0;
         float acc = 0.f, mag = 0.f;
-        // displacement in grid steps (exact integers, then one rounding)
-        const float3 dp = make_float3((float)(int)(t.Pn.x - t.Po.x), (float)(int)(t.Pn.y - t.Po.y),
-                                      (float)(int)(t.Pn.z - t.Po.z));
         int my_self = -1, my_last = 0;
         uint4 my_lv = make_uint4(0, 0, 0, 0);
         const int rows = nrows(t);
@@ -561,9 +563,9 @@ struct Chain {
                     }
                 }
                 if constexpr (P32) {
-                    if (t.type == 0) item32<3>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
-                    else if (t.type == 1) item32<2>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
-                    else item32<1>(t, dp, q[k], cl[k] >= 0, fl[k], acc, mag);
+                    if (t.type == 0) item32<3>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
+                    else if (t.type == 1) item32<2>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
+                    else item32<1>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
                 } else if (cl[k] >= 0 && q[k].w != t.Po.w) {
                     const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q[k].w);
                     if (fl[k] & kOld) pair_terms<false>(t.Po, q[k], a, kk, -1.f, e, ua, de, da);
@@ -589,9 +591,9 @@ struct Chain {
                         }
                     }
                     if constexpr (P32) {
-                        if (t.type == 0) item32<3>(t, dp, qq, true, g, acc, mag);
-                        else if (t.type == 1) item32<2>(t, dp, qq, true, g, acc, mag);
-                        else item32<1>(t, dp, qq, true, g, acc, mag);
+                        if (t.type == 0) item32<3>(t, qq, true, g, acc, mag);
+                        else if (t.type == 1) item32<2>(t, qq, true, g, acc, mag);
+                        else item32<1>(t, qq, true, g, acc, mag);
                     } else if (qq.w != t.Po.w) {
                         const int kk = (int)t.s * kMaxSpecies + (int)tag_species(qq.w);
                         if (g & kOld) pair_terms<false>(t.Po, qq, a, kk, -1.f, e, ua, de, da);
@@ -818,7 +820,7 @@ struct TeamShared {
 // one uncommitted move, so a move is evaluated at most NTEAM - 1 commits
 // ahead of its turn.
 template <bool F32, int G, int NTEAM>
-__global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const __grid_constant__ ChainArgs a)
+__global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
     constexpr int EW = G * NTEAM;
     constexpr int NTH = (EW + 2) * 32;
@@ -827,6 +829,24 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const __grid_
     __shared__ Shared sh;
     __shared__ TeamShared<G> ts[NTEAM];
     __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
+    // this CTA's chain: its arguments copied to shared memory
+    __shared__ __align__(16) ChainArgs a;
+    {
+        const uint32_t *src = (const uint32_t *)(args + blockIdx.x);
+        uint32_t *dst = (uint32_t *)&a;
+        for (int k = threadIdx.x; k < (int)(sizeof(ChainArgs) / 4); k += NTH) dst[k] = src[k];
+        __syncthreads();
+    }
+    if (a.n_moves <= 0) {
+        if (threadIdx.x == 0) {
+            ChainOut &o = *a.out;
+            o.moves_done = 0;
+            o.energy = *a.d_energy;
+            for (int q = 0; q < kMaxSpecies; ++q) o.n[q] = q < a.S ? a.d_n[q] : 0;
+            o.status = 0;
+        }
+        return;
+    }
     Chain<F32> C(a, sh, cnt);
     const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
     const int n = a.n_moves;
@@ -1219,131 +1239,404 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const __grid_
     }
 }
 
-constexpr int kTeamWarps = 7, kTeams = 2;
+// ---------------------------------------------------------------- host side
+// Team shapes the launcher can use: (warps per team, teams).  More teams
+// evaluate more moves ahead (better when moves rarely conflict); larger
+// teams evaluate one move faster (better when N changes often).
+constexpr int kNumConfigs = 4;
+static const int kConfigG[kNumConfigs] = {7, 3, 2, 1};
+static const int kConfigT[kNumConfigs] = {2, 2, 2, 3};
+
+template <bool F32>
+static void *chain_kernel(int config)
+{
+    switch (config) {
+    case 1: return (void *)k_chain<F32, 3, 2>;
+    case 2: return (void *)k_chain<F32, 2, 2>;
+    case 3: return (void *)k_chain<F32, 1, 3>;
+    default: return (void *)k_chain<F32, 7, 2>;
+    }
+}
+
+int chain_threads(int config) { return (kConfigG[config] * kConfigT[config] + 2) * 32; }
+
+// One chain of a launch: its context, random stream, moves and outputs.
+struct ChainJob {
+    gcmc_ctx *ctx;
+    uint64_t seed;
+    uint32_t chain;
+    uint64_t first;
+    int64_t n_moves;
+    gcmc_move_mix mix;
+    gcmc_trace *trace;
+    gcmc_move_stats agg;
+    int64_t done;
+    gcmc_status result;
+};
+
+static void fill_args(ChainArgs &a, const ChainJob &j, ChainOut *out)
+{
+    gcmc_ctx *ctx = j.ctx;
+    const gcmc_move_mix *mix = &j.mix;
+    memset(&a, 0, sizeof(a));
+    a.seed = j.seed;
+    a.first = j.first + (uint64_t)j.done;
+    a.n_moves = (j.result == GCMC_OK) ? (int)std::min<int64_t>(j.n_moves - j.done, 1 << 30) : 0;
+    a.chain = j.chain;
+    a.T = ctx->T;
+    a.ncell = (int)ctx->ncell;
+    a.cap = ctx->cap;
+    a.maxN = ctx->maxN;
+    a.S = ctx->S;
+    a.R2 = ctx->R2;
+    a.rcg = ctx->rcg;
+    {
+        // FP32 r^2 from exact integer separations carries a relative error
+        // below 1e-6 (1 + D / rc); outside this band the FP32 test agrees
+        // with the exact one
+        const double band = 1e-5 * (1.0 + (double)(int64_t)(mix->max_disp * ctx->q) / (double)ctx->rcg);
+        a.r2lo = (float)((double)ctx->R2 * (1.0 - band));
+        a.r2hi = (float)((double)ctx->R2 * (1.0 + band));
+    }
+    a.thr_disp = (unsigned long long)(mix->p_disp * 4294967296.0);
+    a.thr_ins = (unsigned long long)((mix->p_disp + mix->p_ins) * 4294967296.0);
+    const int64_t D = (int64_t)(mix->max_disp * ctx->q);
+    a.D = (int)D;
+    a.span = (uint32_t)(2 * D + 1);
+    a.beta = mix->beta;
+    a.lnV = std::log(ctx->V);
+    for (int s = 0; s < kMaxSpecies; ++s) a.logz[s] = s < ctx->S ? mix->log_z[s] : 0.0;
+    a.tol = ctx->precision == GCMC_FP32 ? 1e-5 : 1e-12;
+    for (int s = 0; s < kMaxSpecies; ++s) a.lnzv_f[s] = (float)(a.logz[s] + a.lnV);
+    a.ff = ctx->ff;
+    a.fd = ctx->fd;
+    a.cell_pos = ctx->cell_pos;
+    a.cell_count = ctx->cell_count;
+    a.pos_by_id = ctx->pos_by_id;
+    a.d_n = ctx->d_n;
+    a.d_energy = ctx->d_energy;
+    a.trace = j.trace ? j.trace + j.done : nullptr;
+    a.out = out;
+}
+
+// Device and pinned buffers of a multi-chain launch.
+struct LaunchBufs {
+    ChainArgs *d_args = nullptr;
+    ChainOut *d_out = nullptr;
+    ChainArgs *h_args = nullptr;  // pinned
+    ChainOut *h_out = nullptr;    // pinned
+    int cap = 0;
+    // a captured round (upload, kernel, download) and what it was captured for
+    cudaGraphExec_t exec = nullptr;
+    void *g_kern = nullptr;
+    int g_K = 0;
+    size_t g_smem = 0;
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        g_kern = nullptr;
+        g_K = 0;
+        g_smem = 0;
+    }
+    ~LaunchBufs()
+    {
+        drop_graph();
+        if (d_args) cudaFree(d_args);
+        if (d_out) cudaFree(d_out);
+        if (h_args) cudaFreeHost(h_args);
+        if (h_out) cudaFreeHost(h_out);
+    }
+    cudaError_t ensure(int k)
+    {
+        if (k <= cap) return cudaSuccess;
+        drop_graph();
+        if (d_args) cudaFree(d_args);
+        if (d_out) cudaFree(d_out);
+        if (h_args) cudaFreeHost(h_args);
+        if (h_out) cudaFreeHost(h_out);
+        d_args = nullptr;
+        d_out = nullptr;
+        h_args = nullptr;
+        h_out = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&d_args, k * sizeof(ChainArgs));
+        if (e == cudaSuccess) e = cudaMalloc(&d_out, k * sizeof(ChainOut));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_args, k * sizeof(ChainArgs));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_out, k * sizeof(ChainOut));
+        if (e == cudaSuccess) cap = k;
+        return e;
+    }
+};
+
+// Runs all jobs to completion in rounds of one launch (one CTA per chain);
+// a chain that would overflow a cell or its capacity stops, is re-laid out
+// and continues in the next round.  Errors are per job.
+static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f32, int config, LaunchBufs &B,
+                            int64_t *launches, std::string *err, bool use_graph = false)
+{
+    const int K = (int)jobs.size();
+    if (K == 0) return GCMC_OK;
+    cudaError_t e = B.ensure(K);
+    if (e != cudaSuccess) {
+        if (err) *err = cudaGetErrorString(e);
+        return GCMC_ERR_CUDA;
+    }
+    size_t smem = 16;
+    for (auto &j : jobs) smem = std::max(smem, ((size_t)j.ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16);
+    void *kern = f32 ? chain_kernel<true>(config) : chain_kernel<false>(config);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return GCMC_ERR_CUDA;
+    }
+    for (int round = 0; round < (1 << 20); ++round) {
+        bool any = false;
+        for (int k = 0; k < K; ++k) {
+            fill_args(B.h_args[k], jobs[k], B.d_out + k);
+            any = any || B.h_args[k].n_moves > 0;
+        }
+        if (!any) break;
+        auto enqueue = [&]() {
+            cudaError_t r = cudaMemcpyAsync(B.d_args, B.h_args, K * sizeof(ChainArgs), cudaMemcpyHostToDevice, st);
+            if (r == cudaSuccess) r = cudaMemsetAsync(B.d_out, 0, K * sizeof(ChainOut), st);
+            if (r == cudaSuccess) {
+                void *kargs[] = {(void *)&B.d_args};
+                r = cudaLaunchKernel(kern, dim3(K), dim3(chain_threads(config)), kargs, smem, st);
+            }
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(B.h_out, B.d_out, K * sizeof(ChainOut), cudaMemcpyDeviceToHost, st);
+            return r;
+        };
+        if (use_graph) {
+            if (!B.exec || B.g_kern != kern || B.g_K != K || B.g_smem != smem) {
+                B.drop_graph();
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e2 = enqueue();
+                    e = cudaStreamEndCapture(st, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&B.exec, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e == cudaSuccess) {
+                    B.g_kern = kern;
+                    B.g_K = K;
+                    B.g_smem = smem;
+                }
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(B.exec, st);
+        } else {
+            e = enqueue();
+        }
+        if (launches) *launches += 1;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            if (err) *err = std::string("chain launch: ") + cudaGetErrorString(e);
+            return GCMC_ERR_CUDA;
+        }
+        for (int k = 0; k < K; ++k) {
+            ChainJob &j = jobs[k];
+            if (B.h_args[k].n_moves <= 0) continue;
+            const ChainOut &o = B.h_out[k];
+            gcmc_ctx *ctx = j.ctx;
+            for (int t = 0; t < 3; ++t) {
+                j.agg.attempted[t] += o.attempted[t];
+                j.agg.accepted[t] += o.accepted[t];
+            }
+            j.agg.flagged += o.flagged;
+            j.agg.moves_done += o.moves_done;
+            j.agg.sum_energy += o.sum_energy;
+            j.agg.sum_n += o.sum_n;
+            j.agg.energy = o.energy;
+            for (int q = 0; q < kMaxSpecies; ++q) {
+                j.agg.n[q] = o.n[q];
+                ctx->n_host[q] = o.n[q];
+            }
+            ctx->energy = o.energy;
+            ctx->compact_valid = false;
+            ctx->order_valid = false;
+            ctx->last_refetch += o.reevaluated;
+            ctx->last_refines += o.refines;
+            j.done += o.moves_done;
+            if (o.status & kStatusNonFinite) j.result = GCMC_ERR_NONFINITE;
+            if (o.status & kStatusTimeout) {
+                j.result = fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_run_moves: a bounded wait inside the chain kernel gave up");
+                continue;
+            }
+            if (o.status & (kStatusCellOverflow | kStatusCapacity)) {
+                const bool grow_cap = (o.status & kStatusCellOverflow) && ctx->cap_req == 0;
+                const bool grow_n = (o.status & kStatusCapacity) && ctx->max_particles_req == 0;
+                if ((o.status & kStatusCellOverflow) && !grow_cap) {
+                    j.result = fail(ctx, GCMC_ERR_CELL_OVERFLOW, "gcmc_run_moves: cell capacity exceeded");
+                    continue;
+                }
+                if ((o.status & kStatusCapacity) && !grow_n) {
+                    j.result = fail(ctx, GCMC_ERR_CAPACITY, "gcmc_run_moves: max_particles exceeded");
+                    continue;
+                }
+                const int ncap = grow_cap ? std::min(65535, ctx->cap + std::max(8, ctx->cap / 2)) : ctx->cap;
+                const int64_t nmax = grow_n ? std::min<int64_t>(1ll << 24, ctx->maxN * 2) : ctx->maxN;
+                gcmc_status rs = relayout(ctx, ncap, nmax);
+                if (rs != GCMC_OK) j.result = rs;
+                continue;
+            }
+            if (o.moves_done == 0) j.result = fail(ctx, GCMC_ERR_CUDA, "gcmc_run_moves: the chain kernel made no progress");
+        }
+        // the grown arrays must be visible to the next round's arguments
+        for (auto &j : jobs) j.ctx->energy_valid = true;
+    }
+    return GCMC_OK;
+}
+
+// Runs the jobs with the given team shape, or -- config < 0 -- first times
+// a short chunk of moves under every shape and runs the rest with the
+// fastest (config returns the choice).  Every shape takes exactly the same
+// moves, so tuning never changes the chain.
+static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, bool f32, int &config,
+                                  LaunchBufs &B, int64_t *launches, std::string *err, bool use_graph,
+                                  double *probe_ms)
+{
+    if (config >= 0) return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+    int64_t remaining = INT64_MAX;
+    for (auto &j : jobs) remaining = std::min<int64_t>(remaining, j.n_moves - j.done);
+    const int64_t chunk = std::min<int64_t>(std::max<int64_t>(remaining / (4 * kNumConfigs), 256), 4096);
+    if (remaining < 2 * chunk * kNumConfigs) {
+        config = 0;
+        return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+    }
+    double best = 1e300;
+    int bc = 0;
+    for (int c = 0; c < kNumConfigs; ++c) {
+        std::vector<int64_t> saved(jobs.size());
+        for (size_t k = 0; k < jobs.size(); ++k) {
+            saved[k] = jobs[k].n_moves;
+            jobs[k].n_moves = std::min<int64_t>(jobs[k].n_moves, jobs[k].done + chunk);
+        }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        gcmc_status r = run_jobs(jobs, st, f32, c, B, launches, err, false);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (size_t k = 0; k < jobs.size(); ++k) jobs[k].n_moves = saved[k];
+        if (r != GCMC_OK) return r;
+        if (probe_ms) probe_ms[c] = ms;
+        if (ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    config = bc;
+    return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+}
+
+static gcmc_status check_chain_fits(gcmc_ctx *ctx)
+{
+    const size_t smem = ((size_t)ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16;
+    if (smem + sizeof(Shared) + sizeof(ChainArgs) + 4096 > ctx->smem_optin)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: too many cells for the on-chip cell counters");
+    if (ctx->T > 1023) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: more than 1023 cells per side");
+    return GCMC_OK;
+}
 
 gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves, const gcmc_move_mix *mix,
                       gcmc_move_stats *stats, gcmc_trace *trace)
 {
-    gcmc_status st;
+    gcmc_status st = check_chain_fits(ctx);
+    if (st != GCMC_OK) return st;
     if (!ctx->energy_valid) {
         st = total_energy(ctx, nullptr);
         if (st != GCMC_OK) return st;
     }
-    gcmc_move_stats agg;
-    memset(&agg, 0, sizeof(agg));
-    st = ensure_red(ctx, (sizeof(ChainOut) + sizeof(double) - 1) / sizeof(double) + 8);
-    if (st != GCMC_OK) return st;
-    ChainOut *d_out = (ChainOut *)ctx->d_red;
-    const size_t smem = ((size_t)ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16;
-    if (smem + sizeof(Shared) + 1024 > ctx->smem_optin)
-        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: too many cells for the on-chip cell counters");
-    if (ctx->T > 1023) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: more than 1023 cells per side");
-    int64_t done_total = 0;
-    gcmc_status result = GCMC_OK;
+    static thread_local LaunchBufs bufs;
+    std::vector<ChainJob> jobs(1);
+    ChainJob &j = jobs[0];
+    memset(&j, 0, sizeof(j));
+    j.ctx = ctx;
+    j.seed = seed;
+    j.chain = 0;
+    j.first = first;
+    j.n_moves = n_moves;
+    j.mix = *mix;
+    j.trace = trace;
+    j.result = GCMC_OK;
     ctx->last_refetch = 0;
     ctx->last_refines = 0;
-    for (int attempt = 0; attempt < (1 << 20) && done_total < n_moves; ++attempt) {
-        ChainArgs a;
-        memset(&a, 0, sizeof(a));
-        a.seed = seed;
-        a.first = first + (uint64_t)done_total;
-        a.n_moves = (int)std::min<int64_t>(n_moves - done_total, 1 << 30);
-        a.chain = 0;
-        a.T = ctx->T;
-        a.ncell = (int)ctx->ncell;
-        a.cap = ctx->cap;
-        a.maxN = ctx->maxN;
-        a.S = ctx->S;
-        a.R2 = ctx->R2;
-        a.rcg = ctx->rcg;
-        {
-            // FP32 r^2 from exact integer separations carries a relative
-            // error below 1e-6 (1 + D / rc); outside this band the FP32 test
-            // agrees with the exact one
-            const double band = 1e-5 * (1.0 + (double)(int64_t)(mix->max_disp * ctx->q) / (double)ctx->rcg);
-            a.r2lo = (float)((double)ctx->R2 * (1.0 - band));
-            a.r2hi = (float)((double)ctx->R2 * (1.0 + band));
+    std::string err;
+    st = run_jobs_tuned(jobs, ctx->stream, ctx->precision == GCMC_FP32, ctx->chain_config, bufs, &ctx->launches,
+                        &err, false, nullptr);
+    if (st != GCMC_OK) return fail(ctx, st, err);
+    if (stats) *stats = j.agg;
+    return j.result;
+}
+
+gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
+                      const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
+                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms)
+{
+    if (K <= 0) return GCMC_OK;
+    const bool f32 = ctxs[0]->precision == GCMC_FP32;
+    for (int k = 0; k < K; ++k) {
+        if (!ctxs[k] || !ctxs[k]->built) {
+            if (err) *err = "gcmc_batch_run_moves: a context has no cells";
+            return GCMC_ERR_STATE;
         }
-        a.thr_disp = (unsigned long long)(mix->p_disp * 4294967296.0);
-        a.thr_ins = (unsigned long long)((mix->p_disp + mix->p_ins) * 4294967296.0);
-        const int64_t D = (int64_t)(mix->max_disp * ctx->q);
-        a.D = (int)D;
-        a.span = (uint32_t)(2 * D + 1);
-        a.beta = mix->beta;
-        a.lnV = std::log(ctx->V);
-        for (int s = 0; s < kMaxSpecies; ++s) a.logz[s] = s < ctx->S ? mix->log_z[s] : 0.0;
-        a.tol = ctx->precision == GCMC_FP32 ? 1e-5 : 1e-12;
-        for (int s = 0; s < kMaxSpecies; ++s) a.lnzv_f[s] = (float)(a.logz[s] + a.lnV);
-        a.ff = ctx->ff;
-        a.fd = ctx->fd;
-        a.cell_pos = ctx->cell_pos;
-        a.cell_count = ctx->cell_count;
-        a.pos_by_id = ctx->pos_by_id;
-        a.d_n = ctx->d_n;
-        a.d_energy = ctx->d_energy;
-        a.trace = trace ? trace + done_total : nullptr;
-        a.out = d_out;
-        const bool f32 = ctx->precision == GCMC_FP32;
-        auto kern = f32 ? k_chain<true, kTeamWarps, kTeams> : k_chain<false, kTeamWarps, kTeams>;
-        GCMC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GCMC_CUDA(ctx, cudaMemsetAsync(d_out, 0, sizeof(ChainOut), ctx->stream));
-        kern<<<1, (kTeamWarps * kTeams + 2) * 32, smem, ctx->stream>>>(a);
-        ctx->launches += 1;
-        GCMC_CUDA(ctx, cudaGetLastError());
-        ChainOut o;
-        GCMC_CUDA(ctx, cudaMemcpyAsync(&o, d_out, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream));
-        GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int t = 0; t < 3; ++t) {
-            agg.attempted[t] += o.attempted[t];
-            agg.accepted[t] += o.accepted[t];
+        if ((ctxs[k]->precision == GCMC_FP32) != f32) {
+            if (err) *err = "gcmc_batch_run_moves: contexts of different precision";
+            return GCMC_ERR_INVALID_ARG;
         }
-        agg.flagged += o.flagged;
-        agg.moves_done += o.moves_done;
-        agg.sum_energy += o.sum_energy;
-        agg.sum_n += o.sum_n;
-        agg.energy = o.energy;
-        for (int q = 0; q < kMaxSpecies; ++q) {
-            agg.n[q] = o.n[q];
-            ctx->n_host[q] = o.n[q];
+        gcmc_status st = check_chain_fits(ctxs[k]);
+        if (st != GCMC_OK) {
+            if (err) *err = ctxs[k]->err;
+            return st;
         }
-        ctx->energy = o.energy;
-        ctx->compact_valid = false;
-        ctx->order_valid = false;
-        ctx->last_refetch += o.reevaluated;
-        ctx->last_refines += o.refines;
-        done_total += o.moves_done;
-        if (o.status & kStatusNonFinite) result = GCMC_ERR_NONFINITE;
-        if (o.status & kStatusTimeout) {
-            result = fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_run_moves: a bounded wait inside the chain kernel gave up");
-            break;
-        }
-        if (o.status & (kStatusCellOverflow | kStatusCapacity)) {
-            const bool grow_cap = (o.status & kStatusCellOverflow) && ctx->cap_req == 0;
-            const bool grow_n = (o.status & kStatusCapacity) && ctx->max_particles_req == 0;
-            if ((o.status & kStatusCellOverflow) && !grow_cap) {
-                result = fail(ctx, GCMC_ERR_CELL_OVERFLOW, "gcmc_run_moves: cell capacity exceeded");
-                break;
+        if (!ctxs[k]->energy_valid) {
+            st = total_energy(ctxs[k], nullptr);
+            if (st != GCMC_OK) {
+                if (err) *err = ctxs[k]->err;
+                return st;
             }
-            if ((o.status & kStatusCapacity) && !grow_n) {
-                result = fail(ctx, GCMC_ERR_CAPACITY, "gcmc_run_moves: max_particles exceeded");
-                break;
-            }
-            const int ncap = grow_cap ? std::min(65535, ctx->cap + std::max(8, ctx->cap / 2)) : ctx->cap;
-            const int64_t nmax = grow_n ? std::min<int64_t>(1ll << 24, ctx->maxN * 2) : ctx->maxN;
-            gcmc_status rs = relayout(ctx, ncap, nmax);
-            if (rs != GCMC_OK) {
-                result = rs;
-                break;
-            }
-            continue;
-        }
-        if (o.moves_done == 0 && a.n_moves > 0) {
-            result = fail(ctx, GCMC_ERR_CUDA, "gcmc_run_moves: the chain kernel made no progress");
-            break;
         }
     }
-    if (stats) *stats = agg;
-    return result;
+    static thread_local LaunchBufs bufs;
+    std::vector<ChainJob> jobs(K);
+    // the chains' own streams first: their earlier work must be complete
+    for (int k = 0; k < K; ++k) {
+        cudaError_t e = cudaStreamSynchronize(ctxs[k]->stream);
+        if (e != cudaSuccess) {
+            if (err) *err = cudaGetErrorString(e);
+            return GCMC_ERR_CUDA;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        ChainJob &j = jobs[k];
+        memset(&j, 0, sizeof(j));
+        j.ctx = ctxs[k];
+        j.seed = seeds[k];
+        j.chain = (uint32_t)k;
+        j.first = first;
+        j.n_moves = n_moves;
+        j.mix = mixes[k];
+        j.result = GCMC_OK;
+        ctxs[k]->last_refetch = 0;
+        ctxs[k]->last_refines = 0;
+    }
+    gcmc_status st = run_jobs_tuned(jobs, stream, f32, config, bufs, launches, err, use_graph && stream != nullptr,
+                                    probe_ms);
+    if (st != GCMC_OK) return st;
+    gcmc_status worst = GCMC_OK;
+    for (int k = 0; k < K; ++k) {
+        if (stats) stats[k] = jobs[k].agg;
+        if (jobs[k].result != GCMC_OK && worst == GCMC_OK) worst = jobs[k].result;
+    }
+    return worst;
 }
 
 }  // namespace gcmc

@@ -415,6 +415,20 @@ gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out)
     return GCMC_OK;
 }
 
+gcmc_status gcmc_set_chain_config(gcmc_ctx *ctx, int32_t config)
+{
+    if (!ctx || config < -1 || config >= kChainConfigs) return GCMC_ERR_INVALID_ARG;
+    ctx->chain_config = config;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_get_chain_config(gcmc_ctx *ctx, int32_t *config)
+{
+    if (!ctx || !config) return GCMC_ERR_INVALID_ARG;
+    *config = ctx->chain_config;
+    return GCMC_OK;
+}
+
 gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined)
 {
     if (!ctx) return GCMC_ERR_INVALID_ARG;
@@ -430,5 +444,104 @@ const char *gcmc_last_error(gcmc_ctx *ctx)
 }
 
 const char *gcmc_version(void) { return "gcmc-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent chains
+// ---------------------------------------------------------------------------
+struct gcmc_batch {
+    std::vector<gcmc_ctx *> ctxs;
+    cudaStream_t stream = nullptr;
+    int config = -1;
+    int64_t launches = 0;
+    double probe_ms[kChainConfigs] = {};
+    std::string err;
+};
+
+extern "C" {
+
+gcmc_status gcmc_batch_create(gcmc_ctx *const *ctxs, int32_t n_chains, gcmc_batch **out)
+{
+    if (!out) return GCMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctxs || n_chains < 1 || n_chains > 65535) return GCMC_ERR_INVALID_ARG;
+    int dev = -1;
+    for (int k = 0; k < n_chains; ++k) {
+        if (!ctxs[k]) return GCMC_ERR_INVALID_ARG;
+        if (k > 0 && ctxs[k]->precision != ctxs[0]->precision) return GCMC_ERR_INVALID_ARG;
+        if (k > 0 && ctxs[k]->device != dev) return GCMC_ERR_INVALID_ARG;
+        dev = ctxs[k]->device;
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == ctxs[k]) return GCMC_ERR_INVALID_ARG;
+    }
+    gcmc_batch *b = new gcmc_batch();
+    b->ctxs.assign(ctxs, ctxs + n_chains);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return GCMC_ERR_CUDA;
+    }
+    *out = b;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_destroy(gcmc_batch *b)
+{
+    if (!b) return GCMC_OK;
+    if (b->stream) {
+        cudaStreamSynchronize(b->stream);
+        cudaStreamDestroy(b->stream);
+    }
+    delete b;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t first_move, int64_t n_moves,
+                                 const gcmc_move_mix *mixes, gcmc_move_stats *stats)
+{
+    if (!b) return GCMC_ERR_INVALID_ARG;
+    if (!seeds || !mixes || n_moves < 0) {
+        b->err = "gcmc_batch_run_moves: bad arguments";
+        return GCMC_ERR_INVALID_ARG;
+    }
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        const gcmc_move_mix *mix = &mixes[k];
+        const double ps = mix->p_disp + mix->p_ins + mix->p_del;
+        if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
+            !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < b->ctxs[k]->L) || !(mix->beta >= 0.0)) {
+            b->err = "gcmc_batch_run_moves: bad move mix";
+            return GCMC_ERR_INVALID_ARG;
+        }
+    }
+    if (n_moves == 0) return GCMC_OK;
+    std::string err;
+    gcmc_status st = run_batch(b->ctxs.data(), (int)b->ctxs.size(), seeds, first_move, n_moves, mixes, stats,
+                               b->config, &b->launches, &err, b->stream, true, b->probe_ms);
+    if (st != GCMC_OK) b->err = err.empty() ? "gcmc_batch_run_moves: a chain failed (see its context)" : err;
+    return st;
+}
+
+gcmc_status gcmc_batch_config(gcmc_batch *b, int32_t set_config, int32_t *config_out, double *probe_ms)
+{
+    if (!b || set_config < -2 || set_config >= kChainConfigs) return GCMC_ERR_INVALID_ARG;
+    if (set_config != -2) b->config = set_config;
+    if (config_out) *config_out = b->config;
+    if (probe_ms)
+        for (int c = 0; c < kChainConfigs; ++c) probe_ms[c] = b->probe_ms[c];
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_launches(gcmc_batch *b, int64_t *out)
+{
+    if (!b || !out) return GCMC_ERR_INVALID_ARG;
+    *out = b->launches;
+    return GCMC_OK;
+}
+
+const char *gcmc_batch_last_error(gcmc_batch *b)
+{
+    if (!b) return "null batch";
+    return b->err.c_str();
+}
 
 }  // extern "C"

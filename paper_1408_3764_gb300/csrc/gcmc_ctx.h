@@ -62,7 +62,8 @@ struct gcmc_ctx {
     bool energy_valid = false;
     int64_t launches = 0;  // kernels this context has launched
     int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
-    int64_t last_refines = 0;  // chain trials decided in FP64 after the FP32 band test (last run)
+    int64_t last_refines = 0;
+    int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)  // chain trials decided in FP64 after the FP32 band test (last run)
 
     std::string err;
 };
@@ -97,5 +98,10 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
 // chain.cu
 gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
+                      const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
+                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms);
+int chain_threads(int config);
+constexpr int kChainConfigs = 4;
 
 }  // namespace gcmc

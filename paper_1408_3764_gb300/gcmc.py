@@ -136,6 +136,15 @@ class Box:
         check(self._lib.gcmc_kernel_launches(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
         return int(out[0])
 
+    def set_chain_config(self, config: int):
+        """Team shape of the chain kernel: 0..3, or -1 = tuned on the next run."""
+        check(self._lib.gcmc_set_chain_config(self._h, int(config)), self._h)
+
+    def chain_config(self) -> int:
+        out = C.c_int32()
+        check(self._lib.gcmc_get_chain_config(self._h, C.byref(out)), self._h)
+        return out.value
+
     def chain_counters(self) -> dict:
         out = np.zeros(2, np.int64)
         check(self._lib.gcmc_chain_counters(self._h, out[0:].ctypes.data_as(C.c_void_p),
@@ -223,6 +232,53 @@ class Box:
                                        pos.ctypes.data_as(C.c_void_p), cc.ctypes.data_as(C.c_void_p),
                                        refs.ctypes.data_as(C.c_void_p), float(energy)), self._h,
               "gcmc_set_state")
+
+
+class Batch:
+    """Independent chains (e.g. the points of an isotherm) run in one launch,
+    one CTA per chain, replayed as a CUDA graph."""
+
+    def __init__(self, boxes: Sequence[Box]):
+        self._lib = load()
+        self.boxes = list(boxes)
+        arr = (C.c_void_p * len(self.boxes))(*[b.handle for b in self.boxes])
+        h = C.c_void_p()
+        check(self._lib.gcmc_batch_create(arr, len(self.boxes), C.byref(h)), None, "gcmc_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gcmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run_moves(self, seeds, first_move: int, n_moves: int, mixes: Sequence[Mix], check_status=True):
+        K = len(self.boxes)
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(K))
+        cm = (MoveMix * K)(*[m.to_c() for m in mixes])
+        st = (MoveStats * K)()
+        rc = self._lib.gcmc_batch_run_moves(self._h, sd.ctypes.data_as(C.c_void_p), int(first_move),
+                                            int(n_moves), cm, st)
+        if check_status and rc != 0:
+            raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
+        return [stats_dict(st[k], self.boxes[k].S) for k in range(K)]
+
+    def config(self, set_config: int = -2):
+        out = C.c_int32()
+        probe = np.zeros(_lib.CHAIN_CONFIGS, np.float64)
+        check(self._lib.gcmc_batch_config(self._h, int(set_config), C.byref(out),
+                                          probe.ctypes.data_as(C.c_void_p)), None, "gcmc_batch_config")
+        return out.value, probe
+
+    def launches(self) -> int:
+        out = np.zeros(1, np.int64)
+        check(self._lib.gcmc_batch_launches(self._h, out.ctypes.data_as(C.c_void_p)), None)
+        return int(out[0])
 
 
 def species_major_order(species) -> np.ndarray:

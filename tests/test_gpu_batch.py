@@ -1,0 +1,123 @@
+"""GPU: batched chains and the chain kernel's team shapes.
+
+Every team shape and the batched launch must take exactly the decisions of
+the sequential chain; each batched chain k is compared with the oracle
+running chain index k (its Philox counter word) on its own."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1408_3764_gb300 import workloads as W  # noqa: E402
+from paper_1408_3764_gb300.gcmc import Batch, Box, Mix  # noqa: E402
+
+
+def _relaxed(n, L, seed, dmin=0.8):
+    rng = np.random.default_rng(seed)
+    pts = np.zeros((0, 3))
+    while len(pts) < n:
+        p = rng.random(3) * L
+        if len(pts):
+            d = pts - p
+            d -= L * np.rint(d / L)
+            if ((d * d).sum(1) < dmin * dmin).any():
+                continue
+        pts = np.vstack([pts, p])
+    return pts
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_team_shapes_take_identical_moves(precision):
+    L = W.box_edge(1500, 0.55)
+    pos = _relaxed(1500, L, 3)
+    mix = Mix(1 / 3, 1 / 3, 1 / 3, 0.3, 1 / 1.2, [-2.7])
+    traces = []
+    for cfg in range(4):
+        b = Box(L, 2.5, [[1.0]], [[1.0]], precision=precision)
+        b.set_chain_config(cfg)
+        b.build_cells(torch.as_tensor(pos), torch.zeros(1500, dtype=torch.int32))
+        _, tr = b.run_moves(21, 0, 8000, mix, trace=True)
+        traces.append((tr, b.get_state()))
+    tol = 1e-5 if precision == "fp32" else 1e-12
+    t0 = traces[0][0]
+    for tr, st in traces[1:]:
+        # decisions and configurations are identical; the energies differ only
+        # in the summation order of the pair terms
+        for k in ("type", "species", "index", "accepted"):
+            assert np.array_equal(tr[k], t0[k]), k
+        ok = np.isfinite(t0["lnA"])
+        assert np.all(np.abs(tr["dU"] - t0["dU"])[ok] <= tol * t0["uabs"][ok] + 1e-300)
+        for x, y in zip(st[:4], traces[0][1][:4]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_autotuned_shape_takes_identical_moves():
+    L = W.box_edge(1200, 0.5)
+    pos = _relaxed(1200, L, 4)
+    mix = Mix(1 / 3, 1 / 3, 1 / 3, 0.3, 1 / 1.2, [-2.7])
+    ref = Box(L, 2.5, [[1.0]], [[1.0]])
+    ref.set_chain_config(0)
+    ref.build_cells(torch.as_tensor(pos), torch.zeros(1200, dtype=torch.int32))
+    _, tr0 = ref.run_moves(5, 0, 60_000, mix, trace=True)
+    auto = Box(L, 2.5, [[1.0]], [[1.0]])
+    auto.set_chain_config(-1)
+    auto.build_cells(torch.as_tensor(pos), torch.zeros(1200, dtype=torch.int32))
+    _, tr1 = auto.run_moves(5, 0, 60_000, mix, trace=True)
+    assert auto.chain_config() in (0, 1, 2, 3)
+    for k in ("type", "species", "index", "accepted"):
+        assert np.array_equal(tr0[k], tr1[k]), k
+    ok = np.isfinite(tr0["lnA"])
+    assert np.all(np.abs(tr0["dU"] - tr1["dU"])[ok] <= 1e-5 * tr0["uabs"][ok] + 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_matches_oracle_per_chain(precision):
+    """Six uneven chains (N 60-1500, rho 0.1-0.6) in one batched launch; chain
+    k equals the oracle's chain k move for move (final state and counts)."""
+    chains = []
+    for k, (n, rho) in enumerate([(60, 0.1), (300, 0.2), (900, 0.6), (1500, 0.45), (200, 0.35), (700, 0.5)]):
+        L = max(W.box_edge(n, rho), 5.01)
+        pos = W.uniform_positions(n, L, 100 + k) if rho < 0.3 else _relaxed(n, L, 100 + k)
+        chains.append((L, pos, float(np.log(rho) - 1.0)))
+    boxes, oracles, mixes, seeds = [], [], [], []
+    for k, (L, pos, lz) in enumerate(chains):
+        n = len(pos)
+        b = Box(L, 2.5, [[1.0]], [[1.0]], precision=precision)
+        b.build_cells(torch.as_tensor(pos), torch.zeros(n, dtype=torch.int32))
+        boxes.append(b)
+        o = O.System(L, 2.5, [[1.0]], [[1.0]])
+        o.build(pos, np.zeros(n, np.int32))
+        o.set_energy(o.total_energy())
+        oracles.append(o)
+        mixes.append(Mix(0.4, 0.3, 0.3, 0.3, 1 / 1.2, [lz]))
+        seeds.append(1000 + 17 * k)
+    batch = Batch(boxes)
+    stats = batch.run_moves(seeds, 0, 20_000, mixes)
+    stats2 = batch.run_moves(seeds, 20_000, 5_000, mixes)  # a second round (graph replay)
+    assert batch.launches() >= 2
+    for k, o in enumerate(oracles):
+        m = mixes[k]
+        tol = 1e-12 if precision == "fp64" else 1e-5
+        to, so = o.run_moves(seeds[k], 0, 25_000, m.p_disp, m.p_ins, m.p_del, m.max_disp, m.beta, m.log_z,
+                             tol=tol, chain=k, trace=True)
+        assert [a + b for a, b in zip(stats[k]["accepted"], stats2[k]["accepted"])] == list(so.accepted)
+        st_o, st_g = o.state(), boxes[k].get_state()
+        for x, y in zip(st_o, st_g[:4]):
+            assert np.array_equal(x, y)
+        # the running energy adds the accepted dU, each within tol * uabs
+        drift = tol * to["uabs"][to["accepted"] == 1].sum() + 1e-9
+        assert abs(stats2[k]["energy"] - so.energy) <= drift
+
+
+def test_batch_rejects_mixed_precision():
+    a = Box(10.0, 2.5, [[1.0]], [[1.0]], precision="fp32")
+    b = Box(10.0, 2.5, [[1.0]], [[1.0]], precision="fp64")
+    with pytest.raises(RuntimeError):
+        Batch([a, b])

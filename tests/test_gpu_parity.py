@@ -336,13 +336,17 @@ def test_chain_parity_full_size_c2(precision):
 
 
 def test_chain_resume_is_bit_exact():
-    """Counter-based moves: [0, a) + [a, b) == [0, b); state export/import resumes."""
+    """Counter-based moves: [0, a) + [a, b) == [0, b); state export/import
+    resumes.  Bit-exact for a fixed team shape (the shape sets the summation
+    order of the pair terms; decisions never depend on it)."""
     L, pos = _relaxed_workload(800, 0.5, 12)
     types = np.zeros(800, np.int32)
     mix = Mix(1 / 3, 1 / 3, 1 / 3, 0.3, 0.8, [-2.6])
     a = Box(L, 2.5, [[1.0]], [[1.0]])
+    a.set_chain_config(1)
     a.build_cells(torch.as_tensor(pos), torch.as_tensor(types))
     b = Box(L, 2.5, [[1.0]], [[1.0]])
+    b.set_chain_config(1)
     b.build_cells(torch.as_tensor(pos), torch.as_tensor(types))
     _, ta = a.run_moves(3, 0, 6000, mix, trace=True)
     _, tb1 = b.run_moves(3, 0, 2500, mix, trace=True)
@@ -350,6 +354,7 @@ def test_chain_resume_is_bit_exact():
     _, tb2 = b.run_moves(3, 2500, 3500, mix, trace=True)
     assert np.array_equal(ta, np.concatenate([tb1, tb2]))
     c = Box(L, 2.5, [[1.0]], [[1.0]])
+    c.set_chain_config(1)
     c.restore(*snap)
     _, tc = c.run_moves(3, 2500, 3500, mix, trace=True)
     assert np.array_equal(tc, tb2)

@@ -177,6 +177,31 @@ gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, in
  * energy: host.  Errors: STATE, CUDA. */
 gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy);
 
+/* The same full-system energy, computed without allocating any memory.  The
+ * paper has no counterpart; this call exists for callers that cannot
+ * allocate device memory where they need the energy: code that runs while
+ * a stream is being captured, code whose device memory is all owned by
+ * another allocator or a fixed budget, and real-time loops that must not
+ * enter the driver's allocator.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: it reads the padded cell layout that gcmc_build_cells
+ * and gcmc_run_moves keep current, and keeps its per-cell partial sums in a
+ * static device array of GCMC_NOALLOC_MAX_CELLS doubles (1 MiB) built into
+ * the library.
+ *   energy: device pointer to one double; written on the context's stream,
+ *           stream-ordered (no host synchronisation; read it after the
+ *           stream reaches the call).  The running energy of the chain is
+ *           not changed.
+ * The first call on a device looks up the static array's device address
+ * (once per device, with the context's device made current for the call);
+ * make that first call before any stream capture begins.  Every call on a
+ * device shares the one array: calls whose kernels overlap on the GPU (on
+ * different streams, or from different contexts) race and give wrong
+ * energies; serialise them.
+ * Errors: INVALID_ARG (NULL or host energy pointer, more than
+ * GCMC_NOALLOC_MAX_CELLS cells), STATE (cells not built), CUDA. */
+#define GCMC_NOALLOC_MAX_CELLS 131072
+gcmc_status gcmc_total_energy_noalloc(gcmc_ctx *ctx, double *energy);
+
 /* Gradient of the full-system energy (Eq. 1 differentiated):
  *   dpos[k]   = dE/dr_k (device, N x 3 FP32, species-major order) or NULL;
  *   deps      = dE/deps[a][b], half of the sum over ordered type pairs (a,b)

@@ -46,6 +46,7 @@ class Geometry(C.Structure):
 
 TRACE_BYTES = 32
 CHAIN_CONFIGS = 4
+NOALLOC_MAX_CELLS = 131072
 
 
 class ProbeResult(C.Structure):
@@ -63,6 +64,7 @@ SIGNATURES = {
     "gcmc_run_moves": (C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_int64, C.POINTER(MoveMix),
                                  C.POINTER(MoveStats), _vp]),
     "gcmc_total_energy": (C.c_int, [_vp, C.POINTER(C.c_double)]),
+    "gcmc_total_energy_noalloc": (C.c_int, [_vp, _vp]),
     "gcmc_energy_grad": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "gcmc_counts": (C.c_int, [_vp, _vp]),
     "gcmc_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),

@@ -245,6 +245,14 @@ gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy)
     return total_energy(ctx, energy);
 }
 
+gcmc_status gcmc_total_energy_noalloc(gcmc_ctx *ctx, double *energy)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!energy) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_total_energy_noalloc: energy is NULL");
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_total_energy_noalloc: cells not built");
+    return total_energy_noalloc(ctx, energy);
+}
+
 gcmc_status gcmc_energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma,
                              double *energy, double *virial)
 {

@@ -92,6 +92,7 @@ gcmc_status relayout(gcmc_ctx *ctx, int new_cap, int64_t new_maxN);
 gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,
                          const int64_t *exclude, int64_t m, double *out, double *out_abs);
 gcmc_status total_energy(gcmc_ctx *ctx, double *energy);
+gcmc_status total_energy_noalloc(gcmc_ctx *ctx, double *energy_dev);
 gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
                         double *virial);
 

@@ -7,6 +7,8 @@
 // FP32 mode: pair terms in FP32, per-lane sums compensated (Neumaier), lane
 // and block sums in FP64.  FP64 mode: everything in FP64.
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "gcmc_ctx.h"
@@ -463,6 +465,161 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
             if (dsigma) dsigma[a * S + b] = h[2 + S * S + a * S + b] / ctx->sigma[a * kMaxSpecies + b];
         }
     return GCMC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free full-system energy.  Some callers may not allocate device
+// memory at the point where they need the energy: code running while a
+// stream is being captured into a CUDA graph (where cudaMalloc is not
+// allowed or not wanted), code under a fixed device-memory budget owned by
+// another allocator, or a real-time loop that must not enter the driver's
+// allocator.  This variant reads the padded cell layout that the chain keeps
+// current (so no compact copy has to be built or grown) and keeps its
+// per-cell partial sums in one file-scope device array instead of the
+// context's scratch.  The array is shared by every call on a device: two
+// calls whose kernels overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+constexpr int64_t kStaticMaxCells = GCMC_NOALLOC_MAX_CELLS;  // T <= 50; 1 MiB of partials
+static __device__ __align__(256) double g_static_partials[kStaticMaxCells];
+
+constexpr int kMaxDevicesStatic = 64;
+static std::mutex g_static_mu;
+static double *g_static_ptr[kMaxDevicesStatic] = {};
+
+// Full-system energy on the padded cell-major layout: one CTA per home cell
+// (grid-stride), the 27 neighbour cells staged in shared memory, partial[c]
+// written for every cell (nothing has to start at zero).
+template <bool F32>
+__global__ void __launch_bounds__(256) k_cell_energy_padded(const uint4 *__restrict__ cell_pos,
+                                                            const int32_t *__restrict__ cell_count, int cap, int T,
+                                                            int64_t ncell, uint64_t R2, const FieldF ff,
+                                                            const FieldD fd, double *__restrict__ partial)
+{
+    __shared__ uint4 stage[kStage];
+    __shared__ int nb_cell[27], nb_end[27];
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
+        if (w == 0) {
+            int cell = 0, n = 0;
+            if (lane < 27) {
+                const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+                const int x = (cx + dx + T) % T, y = (cy + dy + T) % T, z = (cz + dz + T) % T;
+                cell = (z * T + y) * T + x;
+                n = cell_count[cell];
+            }
+            const int inc = warp_inclusive_scan(n);
+            if (lane < 27) {
+                nb_cell[lane] = cell;
+                nb_end[lane] = inc;
+            }
+        }
+        __syncthreads();
+        const int total = nb_end[26];
+        const int nh = cell_count[c];
+        const uint4 *home = cell_pos + c * (int64_t)cap;
+        Acc<F32> acc;
+        for (int base = 0; base < total; base += kStage) {
+            const int nst = min(kStage, total - base);
+            for (int f = threadIdx.x; f < nst; f += blockDim.x) {
+                const int g = base + f;
+                int r = 0;
+                while (g >= nb_end[r]) ++r;
+                stage[f] = cell_pos[(int64_t)nb_cell[r] * cap + (g - (r ? nb_end[r - 1] : 0))];
+            }
+            __syncthreads();
+            for (int i = w; i < nh; i += 8) {
+                const uint4 p = home[i];
+                const int t = (int)tag_species(p.w);
+                for (int f = lane; f < nst; f += 32) pair_acc<F32>(p, stage[f], p.w, R2, t, ff, fd, acc);
+            }
+            __syncthreads();
+        }
+        const double e = warp_sum(acc.ev());
+        if (lane == 0) red[w] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int k = 0; k < 8; ++k) sum += red[k];
+            partial[c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// out[0] = 1/2 * sum of partial[0 .. n) (one block, fixed order): every pair
+// was visited from both of its particles.
+__global__ void __launch_bounds__(1024) k_half_sum(const double *__restrict__ partial, int64_t n,
+                                                   double *__restrict__ out)
+{
+    __shared__ double sh[1024];
+    double sum = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) sum += partial[i];
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = 0.5 * sh[0];
+}
+
+// Device address of the static partials on the current device, looked up
+// once per device (cudaGetSymbolAddress allocates nothing).
+static gcmc_status static_partials(gcmc_ctx *ctx, int device, double **out)
+{
+    if (device < 0 || device >= kMaxDevicesStatic)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_total_energy_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_static_partials)");
+        g_static_ptr[device] = (double *)p;
+    }
+    *out = g_static_ptr[device];
+    return GCMC_OK;
+}
+
+static gcmc_status total_energy_noalloc_on_device(gcmc_ctx *ctx, double *energy_dev)
+{
+    if (ctx->ncell > kStaticMaxCells)
+        return fail(ctx, GCMC_ERR_INVALID_ARG,
+                    "gcmc_total_energy_noalloc: " + std::to_string(ctx->ncell) +
+                        " cells exceed the static scratch of " + std::to_string(kStaticMaxCells) + " cells");
+    cudaPointerAttributes attr{};
+    GCMC_CUDA(ctx, cudaPointerGetAttributes(&attr, energy_dev));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_total_energy_noalloc: energy must be device memory");
+    double *partial = nullptr;
+    gcmc_status st = static_partials(ctx, ctx->device, &partial);
+    if (st != GCMC_OK) return st;
+    const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
+    if (ctx->precision == GCMC_FP32)
+        k_cell_energy_padded<true><<<nb, 256, 0, ctx->stream>>>(ctx->cell_pos, ctx->cell_count, ctx->cap, ctx->T,
+                                                               ctx->ncell, ctx->R2, ctx->ff, ctx->fd, partial);
+    else
+        k_cell_energy_padded<false><<<nb, 256, 0, ctx->stream>>>(ctx->cell_pos, ctx->cell_count, ctx->cap, ctx->T,
+                                                                ctx->ncell, ctx->R2, ctx->ff, ctx->fd, partial);
+    k_half_sum<<<1, 1024, 0, ctx->stream>>>(partial, ctx->ncell, energy_dev);
+    ctx->launches += 2;
+    GCMC_CUDA(ctx, cudaGetLastError());
+    return GCMC_OK;
+}
+
+gcmc_status total_energy_noalloc(gcmc_ctx *ctx, double *energy_dev)
+{
+    int prev = 0;
+    GCMC_CUDA(ctx, cudaGetDevice(&prev));
+    if (prev != ctx->device) GCMC_CUDA(ctx, cudaSetDevice(ctx->device));
+    const gcmc_status st = total_energy_noalloc_on_device(ctx, energy_dev);
+    if (prev != ctx->device) {
+        const cudaError_t e = cudaSetDevice(prev);
+        if (st == GCMC_OK && e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice (restore)");
+    }
+    return st;
 }
 
 }  // namespace gcmc

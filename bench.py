@@ -1,26 +1,37 @@
 #!/usr/bin/env python
 """GCMC moves/s on GB300 -- the benchmark line.
 
-Workload (default): the single-species Lennard-Jones fluid with N = 131,072,
-rho* = 0.6 (L = 60.226), rc = 3.0, T* = 1.5, moves 1/3 displace / insert /
-delete, max displacement 0.3, 10^6 moves per step, FP32 pair terms with FP64
-sums (the FP32-vs-FP64 workload); uniform random start (seeded), synthetic.
+Workload (default, ``--workload isotherm``): the batched isotherm -- 64
+independent single-species Lennard-Jones chains, N0 log-uniform in
+[500, 20000], rho* 0.1 .. 0.7, ln z interpolated along the isotherm, rc 2.5,
+T* 1.2, moves 1/3 displace / insert / delete, max displacement 0.3; FP32 pair
+terms with FP64 sums and FP64 Metropolis decisions; 10^5 moves per chain per
+step, all chains in one graph-replayed launch with the team shape picked by
+the online tuner.  Inputs are seeded uniform random positions (synthetic).
 
-One step = the whole hot path once: bin the input into cells, full-system
-cell-list energy (the chain's starting energy), 10^6 GCMC moves on the
-device, and the full-system gradient (virial) of the final configuration.
-value = moves per second of device time over the K timed steps (inputs
-resident in HBM; L2 flushed between steps by writing a 256 MiB buffer).
-e2e = the same through the public API with the inputs copied from pinned host
-memory and the result read back every step.
+One step = the whole hot path once over every chain: bin the input into
+cells, full-system cell-list energy (the chain's starting energy), 10^5 GCMC
+moves per chain on the device, and the full-system gradient (forces, virial,
+dE/deps, dE/dsigma) of the final configuration.  value = moves of all chains
+per second of device time over the K timed steps (inputs resident in HBM; L2
+flushed between steps by writing a 256 MiB buffer).  e2e = the same through
+the public API with the inputs copied from pinned host memory and the
+results read back every step.
+
+Also reported: the plain FP64 single chain (the 2,048-particle workload),
+the 131,072-particle chain in FP32 and FP64, the batched isotherm in FP64,
+the FP32-vs-FP64 dU agreement of one chain, and the throughput kernels
+(trial energies, full-system energy, gradient, cell build) of the
+million-particle mixture and the 262,144-particle gradient workload.
 
 --impl reference runs the CPU oracle (plain FP64 C) on the host cores as the
-reference arm.
+reference arm, on the same workload and metric.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,6 +45,9 @@ if ROOT not in sys.path:
 
 METRIC = "GCMC moves/sec at 1 GB300 (FP32+batched vs plain FP64) at ΔE rel err ≤1e-5"
 UNIT = "moves/s"
+FLUSH_BYTES = 256 << 20
+DEFAULT_MOVES = {"isotherm": 100_000, "c2": 1_000_000, "c1": 10_000}
+DEFAULT_CPU_MOVES = {"isotherm": 20_000, "c2": 1_000_000, "c1": 10_000}
 
 
 def _args():
@@ -42,12 +56,44 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--moves", type=int, default=1_000_000, help="moves per step")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="isotherm", choices=["isotherm", "c2", "c1"])
+    ap.add_argument("--moves", type=int, default=0, help="moves per chain per step (0: the workload's)")
+    ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--cpu-moves", type=int, default=1_000_000)
-    return ap.parse_args()
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--cpu-moves", type=int, default=0, help="oracle moves per chain in the CPU sample")
+    ap.add_argument("--cpu-workers", type=int, default=0)
+    a = ap.parse_args()
+    if not a.moves:
+        a.moves = DEFAULT_MOVES[a.workload]
+    if not a.cpu_moves:
+        a.cpu_moves = DEFAULT_CPU_MOVES[a.workload]
+    if not a.precision:
+        a.precision = "fp64" if a.workload == "c1" else "fp32"
+    return a
+
+
+def _chains(name):
+    from paper_1408_3764_gb300 import workloads as W
+    if name == "isotherm":
+        return W.isotherm_chains()
+    if name == "c2":
+        return [W.c2_fp32_vs_fp64()]
+    return [W.c1_plain_fp64()]
+
+
+def _workload_config(name, chains, M, precision):
+    ns = [w.n for w in chains]
+    cfg = {"workload": {"isotherm": "batched isotherm: 64 LJ chains, N0 500-20000, rho 0.1-0.7",
+                        "c2": "single-species LJ, N=131072, rho 0.6, rc 3.0, T 1.5",
+                        "c1": "plain single-species LJ, N=2048, rho 0.5, rc 2.5, T 1.2"}[name],
+           "chains": len(chains), "n0_total": int(sum(ns)), "n0_min": int(min(ns)), "n0_max": int(max(ns)),
+           "rho": [round(chains[0].rho, 4), round(chains[-1].rho, 4)], "rc": chains[0].rc,
+           "T": chains[0].temperature, "moves_per_chain_per_step": M,
+           "mix": [chains[0].p_disp, chains[0].p_ins, chains[0].p_del], "max_disp": chains[0].max_disp,
+           "precision": precision, "l2": "flushed (256 MiB write) between steps"}
+    return cfg
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -108,7 +154,62 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# --------------------------------------------------------------- helpers ---
+# ------------------------------------------------------------ CPU oracle ---
+
+def _oracle_chain_step(k_chain, workload, first, n_moves):
+    """One step of the hot path for chain k on the CPU oracle: bin, total
+    energy, n_moves moves, gradient.  Returns (moves, seconds)."""
+    import oracle as O
+    w = _chains(workload)[k_chain]
+    t0 = time.perf_counter()
+    s = O.System(w.L, w.rc, w.eps, w.sigma)
+    s.build(w.positions(), w.types())
+    s.set_energy(s.total_energy())
+    s.run_moves(w.seed, first, n_moves, w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z,
+                chain=k_chain if workload == "isotherm" else 0, trace=False)
+    s.energy_grad()
+    return n_moves, time.perf_counter() - t0
+
+
+class OraclePool:
+    """The oracle's chains spread over host processes (spawned, so that no
+    worker inherits a CUDA context)."""
+
+    def __init__(self, workload, workers):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workload = workload
+        self.n_chains = len(_chains(workload))
+        self.workers = max(1, min(workers, self.n_chains))
+        self.ex = cf.ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"))
+        # start the workers (imports, oracle load) outside any timed region
+        list(self.ex.map(_oracle_chain_step, [0] * self.workers, [workload] * self.workers,
+                         [0] * self.workers, [1] * self.workers))
+
+    def step(self, first, n_moves):
+        t0 = time.perf_counter()
+        ks = list(range(self.n_chains))
+        # largest chains first for a balanced finish
+        ns = [w.n for w in _chains(self.workload)]
+        ks.sort(key=lambda k: -ns[k])
+        res = list(self.ex.map(_oracle_chain_step, ks, [self.workload] * len(ks), [first] * len(ks),
+                               [n_moves] * len(ks)))
+        dt = time.perf_counter() - t0
+        return sum(r[0] for r in res), dt
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def _cpu_workers(a):
+    if a.cpu_workers:
+        return a.cpu_workers
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    return max(1, min(16, n))
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -116,210 +217,344 @@ def _dist():
     return ws, rank
 
 
-def _cpu_baseline(w, n_moves):
-    """The oracle as it stands, on one host core, on a bounded sample."""
-    import oracle as O
-    s = O.System(w.L, w.rc, w.eps, w.sigma)
-    s.build(w.positions(), w.types())
-    s.set_energy(s.total_energy())
-    t0 = time.perf_counter()
-    s.run_moves(w.seed, 0, n_moves, w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z, trace=False)
-    dt = time.perf_counter() - t0
-    return n_moves / dt, dt
-
-
-def _measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except Exception:
-        return {}
-
-
 def run_reference(a):
-    """Reference arm: the CPU oracle timed on the host, same workload/metric."""
+    """Reference arm: the CPU oracle timed on the host cores, same workload
+    and metric; each step is a bounded sample of the workload's step."""
     ws, rank = _dist()
     if rank != 0:
         return 0
-    from paper_1408_3764_gb300 import workloads as W
-    import oracle as O
-    w = W.c2_fp32_vs_fp64()
-    per_step = 200_000
-    s = O.System(w.L, w.rc, w.eps, w.sigma)
-    s.build(w.positions(), w.types())
-    s.set_energy(s.total_energy())
+    chains = _chains(a.workload)
+    pool = OraclePool(a.workload, _cpu_workers(a) if len(chains) > 1 else 1)
+    M = a.cpu_moves
     for k in range(a.warmup):
-        s.run_moves(w.seed, k * per_step, per_step, w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z,
-                    trace=False)
-    t0 = time.perf_counter()
+        pool.step(k * M, M)
+    tot_moves, tot_s = 0, 0.0
     for k in range(a.steps):
-        s.run_moves(w.seed, (a.warmup + k) * per_step, per_step, w.p_disp, w.p_ins, w.p_del, w.max_disp,
-                    w.beta, w.log_z, trace=False)
-    dt = time.perf_counter() - t0
-    v = a.steps * per_step / dt
+        m, dt = pool.step((a.warmup + k) * M, M)
+        tot_moves += m
+        tot_s += dt
+    pool.close()
+    v = tot_moves / tot_s
+    sample = ("%d chain(s) x %d moves per step (bin + total energy + moves + gradient per chain), "
+              "FP64 oracle, %d worker process(es)" % (len(chains), M, pool.workers))
+    cfg = _workload_config(a.workload, chains, M, "fp64")
+    cfg["l2"] = "host"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot_s * 1e3 / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "rho": w.rho, "rc": w.rc, "T": w.temperature,
-                       "moves_per_step": per_step, "l2": "host"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d moves per step of the %s chain (continuing chain)" % (per_step, w.name)},
+            "data": "synthetic (seeded uniform random positions)", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ------------------------------------------------------------- GPU side ---
+
+class Runner:
+    """The chains of one workload on the GPU, and one step of the hot path."""
+
+    def __init__(self, chains, precision, dev, rank, host_inputs=False):
+        import torch
+        from paper_1408_3764_gb300.gcmc import Batch, Box, Mix
+        self.torch = torch
+        self.chains = chains
+        self.dev = dev
+        self.stream = torch.cuda.current_stream(dev)
+        self.boxes = [Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev) for w in chains]
+        self.mixes = [Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z) for w in chains]
+        self.seeds = [w.seed + 7919 * rank for w in chains]  # replicas: independent chains per rank
+        self.batch = Batch(self.boxes) if len(chains) > 1 else None
+        self.pos_h = [torch.from_numpy(w.positions()).pin_memory() for w in chains]
+        self.typ_h = [torch.from_numpy(w.types()).pin_memory() for w in chains]
+        self.pos_d = [p.to(dev) for p in self.pos_h]
+        self.typ_d = [t.to(dev) for t in self.typ_h]
+        self.host_inputs = host_inputs
+        self.chain_ms = 0.0
+
+    def launches(self):
+        n = sum(b.launches() for b in self.boxes)
+        return n + (self.batch.launches() if self.batch else 0)
+
+    def step(self, k, M):
+        torch = self.torch
+        if self.host_inputs:
+            pos = [p.to(self.dev, non_blocking=True) for p in self.pos_h]
+            typ = [t.to(self.dev, non_blocking=True) for t in self.typ_h]
+        else:
+            pos, typ = self.pos_d, self.typ_d
+        energies = []
+        for i, b in enumerate(self.boxes):
+            b.build_cells(pos[i], typ[i])
+            energies.append(b.total_energy())
+        if self.batch is None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            stats = [self.boxes[0].run_moves(self.seeds[0], k * M, M, self.mixes[0])]
+            e1.record(self.stream)
+            e1.synchronize()
+            self.chain_ms = e0.elapsed_time(e1)
+        else:
+            stats = self.batch.run_moves(self.seeds, k * M, M, self.mixes)
+            self.chain_ms = self.batch.device_ms()
+        grads = [b.energy_grad(want_pos=True) for b in self.boxes]
+        return stats, grads, energies
+
+    def close(self):
+        if self.batch:
+            self.batch.close()
+
+
+def _time_steps(runner, first_step, steps, M, flush):
+    torch = runner.torch
+    times, chain = [], []
+    last = None
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(runner.stream)
+        last = runner.step(first_step + k, M)
+        e1.record(runner.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        chain.append(runner.chain_ms)
+    return times, chain, last
+
+
+def _single_chain_rate(w, precision, M, dev, flush):
+    """Moves/s of one chain (device time of the chain kernel) after a warm-up step."""
+    r = Runner([w], precision, dev, 0)
+    r.step(0, min(M, 20_000))
+    times, chain, _ = _time_steps(r, 1, 1, M, flush)
+    r.close()
+    return {"moves_per_s": M / (chain[0] / 1e3), "step_moves_per_s": M / (times[0] / 1e3), "moves": M,
+            "precision": precision, "n": w.n}
+
+
+def _fp32_vs_fp64_agreement(w, M, dev):
+    """The same chain in FP32 and FP64 mode on the GPU: identical decisions,
+    dU difference relative to uabs (the scale of the pair terms)."""
+    import numpy as np
+    import torch
+    from paper_1408_3764_gb300.gcmc import Box, Mix
+    tr = {}
+    for prec in ("fp32", "fp64"):
+        b = Box(w.L, w.rc, w.eps, w.sigma, precision=prec, device=dev)
+        b.build_cells(torch.from_numpy(w.positions()).to(dev), torch.from_numpy(w.types()).to(dev))
+        _, t = b.run_moves(w.seed, 0, M, Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z),
+                           trace=True)
+        tr[prec] = t
+    a, b = tr["fp32"], tr["fp64"]
+    same = all(np.array_equal(a[k], b[k]) for k in ("type", "species", "index", "accepted"))
+    ok = np.isfinite(b["lnA"]) & (b["uabs"] > 0)
+    rel = np.abs(a["dU"] - b["dU"])[ok] / b["uabs"][ok]
+    return {"chain_n0": w.n, "rho": w.rho, "moves": M, "identical_decisions": bool(same),
+            "max_dU_err_over_uabs": float(rel.max()) if rel.size else 0.0,
+            "flagged_and_refined": int((a["flagged"] & 1).sum())}
+
+
+def _kernel_figures(dev, flush, sm_mhz):
+    """Throughput kernels on the million-particle mixture and the gradient
+    workload: trial energies, full-system energy, gradient, cell build."""
+    import torch
+    from paper_1408_3764_gb300 import workloads as W
+    from paper_1408_3764_gb300.gcmc import Box, Mix
+    out = {}
+    fp32_peak = 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12  # TFLOP/s, FP32 FMA lanes x clock
+
+    def ev_time(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    w = W.c3_mixture_1m()
+    pos = torch.from_numpy(w.positions()).to(dev)
+    typ = torch.from_numpy(w.types()).to(dev)
+    b = Box(w.L, w.rc, w.eps, w.sigma, precision="fp32", device=dev)
+    ms_build = ev_time(lambda: b.build_cells(pos, typ))
+    b.build_cells(pos, typ)
+    # relaxed by 10^4 displacements, as the workload states
+    b.run_moves(w.seed, 0, 10_000, Mix(1.0, 0.0, 0.0, w.max_disp, w.beta, w.log_z))
+    g = b.geometry()
+    ncell, N = g["n_cells"], w.n
+    rho = N / w.L ** 3
+    cand = 27.0 * N / ncell                       # candidates per trial point (27 cells)
+    inr = 4.0 / 3.0 * math.pi * w.rc ** 3 * rho  # partners within rc per point
+    m = 1_000_000
+    tp, ts = W.insertion_points(m, w.L, 2, 7)
+    tpd = torch.from_numpy(tp).to(dev)
+    tsd = torch.from_numpy(ts).to(dev)
+    tout = torch.empty(m, dtype=torch.float64, device=dev)
+    b.trial_energy_raw(tpd, tsd, tout)
+    ms_trial = ev_time(lambda: b.trial_energy_raw(tpd, tsd, tout))
+    ms_total = ev_time(lambda: b.total_energy())
+
+    # FLOP model: 6 per candidate (separation, squared distance, cutoff) +
+    # 11 per pair within rc (1/r^2, s^6, s^12 - s^6, 4 eps, sums)
+    def alu(points, ms):
+        fl = points * (6.0 * cand + 11.0 * inr)
+        ach = fl / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "flop_model": "6 per candidate + 11 per pair within rc"}
+
+    out["trial_energy_mixture_1m"] = {"points": m, "ms": ms_trial, "points_per_s": m / (ms_trial / 1e3),
+                                      "candidates_per_point": cand, "pairs_in_rc_per_point": inr,
+                                      "roofline": alu(m, ms_trial)}
+    out["total_energy_mixture_1m"] = {"particles": N, "ms": ms_total, "roofline": alu(N, ms_total)}
+    out["cell_build_mixture_1m"] = {"particles": N, "ms": ms_build, "particles_per_s": N / (ms_build / 1e3)}
+    del b, tpd, tsd, tout
+    w5 = W.c5_gradient()
+    b5 = Box(w5.L, w5.rc, w5.eps, w5.sigma, precision="fp32", device=dev)
+    b5.build_cells(torch.from_numpy(w5.positions()).to(dev), torch.from_numpy(w5.types()).to(dev))
+    ms_grad = ev_time(lambda: b5.energy_grad(want_pos=True))
+    out["energy_grad_262k"] = {"particles": w5.n, "ms": ms_grad, "particles_per_s": w5.n / (ms_grad / 1e3)}
+    return out
 
 
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    import numpy as np
+    import ctypes as C
+
     import torch
     import torch.distributed as dist
 
-    from paper_1408_3764_gb300 import _lib, workloads as W
-    from paper_1408_3764_gb300.gcmc import Box, Mix
+    from paper_1408_3764_gb300 import _lib
+    from paper_1408_3764_gb300 import workloads as W
 
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    chains = _chains(a.workload)
+    # the CPU baseline's worker processes are spawned before the first GPU call
+    pool = None
+    if rank == 0 and not a.no_cpu_baseline:
+        pool = OraclePool(a.workload, _cpu_workers(a) if len(chains) > 1 else 1)
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    w = W.c2_fp32_vs_fp64()
     M = a.moves
-    mix = Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z)
-    pos_h = torch.from_numpy(w.positions()).pin_memory()
-    typ_h = torch.from_numpy(w.types()).pin_memory()
-    pos_d = pos_h.to(dev)
-    typ_d = typ_h.to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    run = Runner(chains, a.precision, dev, rank)
 
-    def make_box(precision):
-        return Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev)
-
-    box = make_box(a.precision)
-    seed = w.seed + 7919 * rank  # replicas: independent chains per rank
-
-    def step(b, k, pos, typ, timers=None):
-        b.build_cells(pos, typ)
-        b.total_energy()
-        if timers is not None:
-            timers[0].record(stream)
-        st = b.run_moves(seed, k * M, M, mix)
-        if timers is not None:
-            timers[1].record(stream)
-        g = b.energy_grad(want_pos=True)
-        return st, g
-
-    # warm-up
     for k in range(a.warmup):
-        step(box, k, pos_d, typ_d)
+        run.step(k, M)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    launches0 = box.launches()
-    times, chain_times = [], []
-    last = None
+    launches0 = run.launches()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        for k in range(a.steps):
-            flush.fill_(k & 0xFF)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            c = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            e0.record(stream)
-            last = step(box, a.warmup + k, pos_d, typ_d, timers=c)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            chain_times.append(c[0].elapsed_time(c[1]))
+        times, chain_times, last = _time_steps(run, a.warmup, a.steps, M, flush)
         torch.cuda.synchronize()
-    launches = box.launches() - launches0
-    counters = box.chain_counters()
+    if ws > 1:
+        dist.barrier()
+    launches = run.launches() - launches0
+    clocks = clk.summary()
     total_ms = sum(times)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = ws * a.steps * M / (total_ms / 1e3)
+    K = len(chains)
+    value = ws * a.steps * K * M / (total_ms / 1e3)
+    stats = last[0]
+    tuned = run.batch.config() if run.batch else (run.boxes[0].chain_config(), None)
 
-    # end to end through the public API: host inputs, result read back
-    e2e_box = make_box(a.precision)
-    for k in range(1):
-        step(e2e_box, k, pos_h.to(dev, non_blocking=True), typ_h.to(dev, non_blocking=True))
+    # end to end through the public API: host inputs, results read back
+    e2e_run = Runner(chains, a.precision, dev, rank, host_inputs=True)
+    e2e_run.step(0, M)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2d = d2h = 0
     for k in range(a.steps):
-        pd = pos_h.to(dev, non_blocking=True)
-        td = typ_h.to(dev, non_blocking=True)
-        h2d += pd.numel() * 8 + td.numel() * 4
-        st, g = step(e2e_box, a.warmup + k, pd, td)
-        res = torch.tensor([st["energy"], g["virial"]]).numpy()  # stats arrive on the host
-        d2h += 8 * 2 + 8 * 13
+        e2e_run.step(a.warmup + k, M)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": a.steps * M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // a.steps,
-           "d2h_bytes_per_step": d2h // a.steps}
+    e2e_run.close()
+    h2d = sum(w.n * 3 * 8 + w.n * 4 for w in chains)
+    S = len(chains[0].log_z)
+    d2h = K * (8 + C.sizeof(_lib.MoveStats) + 8 * (2 + 2 * S * S))
+    e2e = {"value": ws * a.steps * K * M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
 
-    # latency floor of one chain (roofline of the dominant kernel)
+    # roofline of the dominant kernel: the chain kernel against the latency
+    # floor of one move (one dependent L2 round trip), one chain per CTA
     probe = _lib.ProbeResult()
-    import ctypes as C
-    st_ws = 8 << 20
-    rc = _lib.load().gcmc_probe_latency(C.c_void_p(stream.cuda_stream), st_ws, C.byref(probe))
+    rc = _lib.load().gcmc_probe_latency(C.c_void_p(run.stream.cuda_stream), 8 << 20, C.byref(probe))
     chain_ms = sum(chain_times) / len(chain_times)
-    achieved = M / (chain_ms / 1e3)
-    peak = 1e9 / probe.floor_ns if rc == 0 and probe.floor_ns > 0 else None
+    achieved = K * M / (chain_ms / 1e3)
+    peak = K * 1e9 / probe.floor_ns if rc == 0 and probe.floor_ns > 0 else None
     roofline = {"bound": "latency", "achieved": achieved, "peak": peak, "unit": UNIT,
-                "frac": (achieved / peak) if peak else None, "traffic": None,
-                "kernel": "k_chain", "floor_ns": probe.floor_ns,
-                "floor_parts_ns": {"l2_hop": probe.l2_hop_ns, "sync_round": probe.sync_round_ns,
-                                   "philox": probe.philox_ns, "log": probe.log_ns},
-                "peak_source": "measured by gcmc_probe_latency in this run (2 dependent L2 hops + "
-                               "CTA reduction/broadcast + Philox + FP64 log)"}
+                "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": "k_chain",
+                "launch_ms": chain_ms,
+                "floor_ns_per_move": probe.floor_ns,
+                "context_ns": {"l2_hop": probe.l2_hop_ns, "cta_reduction": probe.sync_round_ns,
+                               "philox_2_blocks": probe.philox_ns, "fp64_log": probe.log_ns},
+                "peak_source": "measured in this run by gcmc_probe_latency: %d chains x 1 / (one dependent "
+                               "L2 round trip per move)" % K}
 
-    compare = {}
-    if not a.no_compare and rank == 0:
-        other = "fp64" if a.precision == "fp32" else "fp32"
-        b2 = make_box(other)
-        step(b2, 0, pos_d, typ_d)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        c = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        flush.fill_(1)
-        e0.record(stream)
-        st2, _ = step(b2, 1, pos_d, typ_d, timers=c)
-        e1.record(stream)
-        e1.synchronize()
-        compare = {"%s_moves_per_s" % other: M / (e0.elapsed_time(e1) / 1e3),
-                   "%s_chain_moves_per_s" % other: M / (c[0].elapsed_time(c[1]) / 1e3)}
+    compare, agreement, kernels = {}, None, None
+    if rank == 0 and not a.no_compare:
+        if a.workload != "c1":
+            compare["plain_fp64_single_chain_2048"] = _single_chain_rate(W.c1_plain_fp64(), "fp64", 10_000, dev,
+                                                                         flush)
+        if a.workload != "c2":
+            for prec in ("fp32", "fp64"):
+                compare["single_chain_131072_" + prec] = _single_chain_rate(W.c2_fp32_vs_fp64(), prec, 200_000,
+                                                                            dev, flush)
+        if a.workload == "isotherm":
+            other = "fp64" if a.precision == "fp32" else "fp32"
+            r2 = Runner(chains, other, dev, 0)
+            r2.step(0, M)
+            t2, c2, _ = _time_steps(r2, 1, 1, M, flush)
+            r2.close()
+            compare["isotherm_batched_" + other] = {"moves_per_s": K * M / (c2[0] / 1e3),
+                                                     "step_moves_per_s": K * M / (t2[0] / 1e3)}
+        base = compare.get("plain_fp64_single_chain_2048")
+        if base:
+            compare["value_over_plain_fp64_single_chain"] = value / base["step_moves_per_s"]
+        agreement = _fp32_vs_fp64_agreement(chains[-1], 20_000, dev)
+    if rank == 0 and not a.no_kernels:
+        kernels = _kernel_figures(dev, flush, clocks.get("sm_mhz"))
 
     cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
-        v, dt = _cpu_baseline(w, a.cpu_moves)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d moves of the %s chain, FP64 oracle, 1 core (%.1f s)" % (a.cpu_moves, w.name, dt)}
+    if pool is not None:
+        m, dt = pool.step(0, a.cpu_moves)
+        pool.close()
+        cpu = {"value": m / dt, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+               "sample": "%d chain(s) x %d moves (bin + total energy + moves + gradient per chain), FP64 "
+                         "oracle, %d worker process(es), %.1f s wall" % (K, a.cpu_moves, pool.workers, dt)}
 
     if rank == 0:
-        st = last[0]
+        acc = [sum(s["accepted"][i] for s in stats) / max(1, sum(s["attempted"][i] for s in stats))
+               for i in range(3)]
+        cfg = _workload_config(a.workload, chains, M, a.precision)
+        cfg["parallelism"] = ("replicas x%d" % ws) if ws > 1 else ("batched, one CTA per chain" if K > 1
+                                                                    else "single chain")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64",
-                "data": "synthetic",
-                "config": {"workload": w.name, "n": w.n, "rho": w.rho, "L": w.L, "rc": w.rc, "T": w.temperature,
-                           "moves_per_step": M, "mix": [w.p_disp, w.p_ins, w.p_del], "max_disp": w.max_disp,
-                           "precision": a.precision, "l2": "flushed (256 MiB write) between steps",
-                           "parallelism": "replicas" if ws > 1 else "single chain"},
-                "chain_moves_per_s": achieved,
-                "acceptance": [st["accepted"][i] / max(1, st["attempted"][i]) for i in range(3)],
-                "final_n": st["n"], "flagged": st["flagged"], "chain_counters_last_step": counters,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk.summary(), "compare": compare}
+                "data": "synthetic (seeded uniform random positions)", "config": cfg,
+                "chain_moves_per_s": achieved, "team_shape": tuned[0],
+                "acceptance": acc, "final_n_total": int(sum(sum(s["n"]) for s in stats)),
+                "flagged": int(sum(s["flagged"] for s in stats)),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "compare": compare, "fp32_vs_fp64": agreement, "kernels": kernels}
         print(json.dumps(line))
+    run.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

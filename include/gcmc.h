@@ -289,6 +289,13 @@ gcmc_status gcmc_batch_config(gcmc_batch *batch, int32_t set_config, int32_t *co
 /* Chain-kernel launches (graph replays included) made by the batch. */
 gcmc_status gcmc_batch_launches(gcmc_batch *batch, int64_t *out);
 
+/* Device time in ms of the chain-kernel launches of the last
+ * gcmc_batch_run_moves (tuning launches included), taken with CUDA events on
+ * the batch's stream around each launch; each launch's few-hundred-byte
+ * argument upload and result download fall inside.  ms: host.
+ * Errors: INVALID_ARG. */
+gcmc_status gcmc_batch_device_ms(gcmc_batch *batch, double *ms);
+
 const char *gcmc_batch_last_error(gcmc_batch *batch);
 
 /* Library version string. */

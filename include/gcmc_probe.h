@@ -3,12 +3,15 @@
  * chain on the GPU (measurement aid; the paper has no counterpart).
  *
  * A single chain is a sequence of dependent steps: every move needs the
- * previous move's outcome.  Its throughput is bounded below by the
- * dependent latencies one move cannot avoid: two dependent global-memory
- * round trips served from L2 (the trial particle's record, then its
- * neighbour cells), one CTA-wide reduction with broadcast, the counter-based
- * random draw and the logarithm of the Metropolis test.  gcmc_probe_latency
- * measures each on the current device.
+ * previous move's outcome.  Trial evaluations can run ahead of the chain
+ * (speculatively, on the configuration as it stands), but the commit of a
+ * move cannot: its decision and cell update must reach the memory the next
+ * evaluations read before a move that depends on it can be decided.  The
+ * floor of one chain is therefore taken as one dependent global-memory round
+ * trip served from L2 per move.  gcmc_probe_latency measures it on the
+ * current device, with the other per-move latencies of a non-speculative
+ * chain (a CTA-wide reduction with broadcast, the counter-based random draw,
+ * an FP64 logarithm) for context.
  */
 #ifndef GCMC_PROBE_H
 #define GCMC_PROBE_H
@@ -26,7 +29,7 @@ typedef struct {
     double sync_round_ns;  /* 256-thread CTA: FP64 warp reductions + 2 barriers + broadcast */
     double philox_ns;      /* two dependent Philox4x32-10 blocks (one move's words) */
     double log_ns;         /* one dependent FP64 log */
-    double floor_ns;       /* 2 * l2_hop + sync_round + philox + log */
+    double floor_ns;       /* l2_hop: one dependent round trip per committed move */
     int64_t working_set_bytes;
 } gcmc_probe_result;
 

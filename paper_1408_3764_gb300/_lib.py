@@ -79,6 +79,7 @@ SIGNATURES = {
     "gcmc_batch_run_moves": (C.c_int, [_vp, _vp, C.c_uint64, C.c_int64, _vp, _vp]),
     "gcmc_batch_config": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "gcmc_batch_launches": (C.c_int, [_vp, _vp]),
+    "gcmc_batch_device_ms": (C.c_int, [_vp, C.POINTER(C.c_double)]),
     "gcmc_batch_last_error": (C.c_char_p, [_vp]),
     "gcmc_last_error": (C.c_char_p, [_vp]),
     "gcmc_version": (C.c_char_p, []),

@@ -1331,6 +1331,7 @@ struct LaunchBufs {
     void *g_kern = nullptr;
     int g_K = 0;
     size_t g_smem = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // launch timing
     void drop_graph()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1342,6 +1343,8 @@ struct LaunchBufs {
     ~LaunchBufs()
     {
         drop_graph();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
         if (d_args) cudaFree(d_args);
         if (d_out) cudaFree(d_out);
         if (h_args) cudaFreeHost(h_args);
@@ -1372,12 +1375,19 @@ struct LaunchBufs {
 // Runs all jobs to completion in rounds of one launch (one CTA per chain);
 // a chain that would overflow a cell or its capacity stops, is re-laid out
 // and continues in the next round.  Errors are per job.
+// dev_ms (may be NULL) accumulates the device time of the launches, taken
+// with CUDA events on st around each launch (argument upload and result
+// download of a few hundred bytes included).
 static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f32, int config, LaunchBufs &B,
-                            int64_t *launches, std::string *err, bool use_graph = false)
+                            int64_t *launches, std::string *err, bool use_graph = false, double *dev_ms = nullptr)
 {
     const int K = (int)jobs.size();
     if (K == 0) return GCMC_OK;
     cudaError_t e = B.ensure(K);
+    if (e == cudaSuccess && dev_ms && !B.ev0) {
+        e = cudaEventCreate(&B.ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&B.ev1);
+    }
     if (e != cudaSuccess) {
         if (err) *err = cudaGetErrorString(e);
         return GCMC_ERR_CUDA;
@@ -1408,6 +1418,11 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
                 r = cudaMemcpyAsync(B.h_out, B.d_out, K * sizeof(ChainOut), cudaMemcpyDeviceToHost, st);
             return r;
         };
+        if (dev_ms) e = cudaEventRecord(B.ev0, st);
+        if (e != cudaSuccess) {
+            if (err) *err = std::string("cudaEventRecord: ") + cudaGetErrorString(e);
+            return GCMC_ERR_CUDA;
+        }
         if (use_graph) {
             if (!B.exec || B.g_kern != kern || B.g_K != K || B.g_smem != smem) {
                 B.drop_graph();
@@ -1431,7 +1446,13 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
             e = enqueue();
         }
         if (launches) *launches += 1;
+        if (e == cudaSuccess && dev_ms) e = cudaEventRecord(B.ev1, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && dev_ms) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, B.ev0, B.ev1);
+            *dev_ms += ms;
+        }
         if (e != cudaSuccess) {
             if (err) *err = std::string("chain launch: ") + cudaGetErrorString(e);
             return GCMC_ERR_CUDA;
@@ -1496,15 +1517,15 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
 // moves, so tuning never changes the chain.
 static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, bool f32, int &config,
                                   LaunchBufs &B, int64_t *launches, std::string *err, bool use_graph,
-                                  double *probe_ms)
+                                  double *probe_ms, double *dev_ms = nullptr)
 {
-    if (config >= 0) return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+    if (config >= 0) return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);
     int64_t remaining = INT64_MAX;
     for (auto &j : jobs) remaining = std::min<int64_t>(remaining, j.n_moves - j.done);
     const int64_t chunk = std::min<int64_t>(std::max<int64_t>(remaining / (4 * kNumConfigs), 256), 4096);
     if (remaining < 2 * chunk * kNumConfigs) {
         config = 0;
-        return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+        return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);
     }
     double best = 1e300;
     int bc = 0;
@@ -1518,7 +1539,7 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
-        gcmc_status r = run_jobs(jobs, st, f32, c, B, launches, err, false);
+        gcmc_status r = run_jobs(jobs, st, f32, c, B, launches, err, false, dev_ms);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1534,7 +1555,7 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
         }
     }
     config = bc;
-    return run_jobs(jobs, st, f32, config, B, launches, err, use_graph);
+    return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);
 }
 
 static gcmc_status check_chain_fits(gcmc_ctx *ctx)
@@ -1579,8 +1600,9 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
 
 gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
-                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms)
+                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms, double *dev_ms)
 {
+    if (dev_ms) *dev_ms = 0.0;
     if (K <= 0) return GCMC_OK;
     const bool f32 = ctxs[0]->precision == GCMC_FP32;
     for (int k = 0; k < K; ++k) {
@@ -1629,7 +1651,7 @@ gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint6
         ctxs[k]->last_refines = 0;
     }
     gcmc_status st = run_jobs_tuned(jobs, stream, f32, config, bufs, launches, err, use_graph && stream != nullptr,
-                                    probe_ms);
+                                    probe_ms, dev_ms);
     if (st != GCMC_OK) return st;
     gcmc_status worst = GCMC_OK;
     for (int k = 0; k < K; ++k) {

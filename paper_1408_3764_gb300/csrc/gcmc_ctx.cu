@@ -464,6 +464,7 @@ struct gcmc_batch {
     int config = -1;
     int64_t launches = 0;
     double probe_ms[kChainConfigs] = {};
+    double last_ms = 0.0;  // device time of the last call's chain launches
     std::string err;
 };
 
@@ -524,7 +525,7 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
     if (n_moves == 0) return GCMC_OK;
     std::string err;
     gcmc_status st = run_batch(b->ctxs.data(), (int)b->ctxs.size(), seeds, first_move, n_moves, mixes, stats,
-                               b->config, &b->launches, &err, b->stream, true, b->probe_ms);
+                               b->config, &b->launches, &err, b->stream, true, b->probe_ms, &b->last_ms);
     if (st != GCMC_OK) b->err = err.empty() ? "gcmc_batch_run_moves: a chain failed (see its context)" : err;
     return st;
 }
@@ -543,6 +544,13 @@ gcmc_status gcmc_batch_launches(gcmc_batch *b, int64_t *out)
 {
     if (!b || !out) return GCMC_ERR_INVALID_ARG;
     *out = b->launches;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_device_ms(gcmc_batch *b, double *ms)
+{
+    if (!b || !ms) return GCMC_ERR_INVALID_ARG;
+    *ms = b->last_ms;
     return GCMC_OK;
 }
 

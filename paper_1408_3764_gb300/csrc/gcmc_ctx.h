@@ -101,7 +101,8 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
                       const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
 gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
-                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms);
+                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms,
+                      double *dev_ms);
 int chain_threads(int config);
 constexpr int kChainConfigs = 4;
 

@@ -146,7 +146,7 @@ extern "C" gcmc_status gcmc_probe_latency(void *stream, int64_t bytes, gcmc_prob
             k_probe_log<<<1, 1, 0, s>>>(c->n, (double *)c->sink);
         }, &la);
     out->log_ns = ms * 1e6 / nlog;
-    out->floor_ns = 2.0 * out->l2_hop_ns + out->sync_round_ns + out->philox_ns + out->log_ns;
+    out->floor_ns = out->l2_hop_ns;
     out->working_set_bytes = nslots * kHopStride * 4;
     if (d_next) cudaFree(d_next);
     if (d_sink) cudaFree(d_sink);

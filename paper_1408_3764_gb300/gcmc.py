@@ -280,6 +280,12 @@ class Batch:
         check(self._lib.gcmc_batch_launches(self._h, out.ctypes.data_as(C.c_void_p)), None)
         return int(out[0])
 
+    def device_ms(self) -> float:
+        """Device time of the chain launches of the last run_moves call."""
+        out = C.c_double()
+        check(self._lib.gcmc_batch_device_ms(self._h, C.byref(out)), None)
+        return out.value
+
 
 def species_major_order(species) -> np.ndarray:
     """Input indices listed in species-major order (species 0 first, input

@@ -5,14 +5,18 @@
 //
 // One CTA owns one chain.  Its warps have three roles:
 //
-//  * evaluators (warps 1..EW): warp w evaluates moves w-1, w-1+EW, ...
-//    Each evaluation is speculative: it reads the configuration as it
-//    stands when the evaluation starts (after `committed` moves) and
-//    produces the trial (particle, old/new position, cells), its energy
-//    change dU (27 neighbour cells, Algorithms 6 and 7; the union of both
-//    neighbourhoods for a displacement that changes cell), the error scale
-//    uabs, and the slots the update will need.  Pair terms are FP32 (or FP64)
-//    from exact integer separations; sums are float-float;
+//  * evaluator teams (warps 1..G*NTEAM): team k evaluates moves k, k + NTEAM,
+//    ..., each as soon as fewer than LOOK moves separate it from the
+//    committer.  An evaluation is speculative: it reads the configuration as
+//    it stands when it starts (after `c0` committed moves) and produces the
+//    trial (particle, old/new position, cells), its energy change dU (the 27
+//    neighbour cells, Algorithms 6 and 7; the union of both neighbourhoods
+//    for a displacement that changes cell), the error scale uabs, and the
+//    slots the update will need.  A lane owns up to two cells of the trial's
+//    work list and the team's warps split the slots of every cell; each warp
+//    leaves its sums in the move's slot and the committer adds them in a
+//    fixed order.  Pair terms are FP32 (or FP64) from exact integer
+//    separations;
 //  * the committer (warp 0) takes the moves strictly in order.  A move is
 //    valid when no move committed after its evaluation started touched one
 //    of its cells, changed N (which selects the particle of a displacement
@@ -50,7 +54,7 @@ struct ChainOut {
     double sum_n;
     long long n[kMaxSpecies];
     int status;
-    int pad;
+    int pad;                // which waits gave up (1 leader, 2 committer, 4 keeper)
     long long reevaluated;  // moves evaluated again by the committer
     long long refines;      // trials decided in FP64 after the FP32 band test
 };
@@ -89,7 +93,22 @@ struct ChainArgs {
 constexpr int kRS = 32;       // move slots in flight (logs and book entries too)
 constexpr int kRW = 128;      // words ring
 constexpr int kFill = 32;     // words filled per keeper round
-constexpr long long kSpinMax = 1ll << 27;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a wait gives up after 1 s
+
+// A bounded wait: expired() turns true once the wait has lasted kWaitNs
+// (global timer, read every 256 polls).
+struct Wait {
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    __device__ __forceinline__ bool expired()
+    {
+        if ((++polls & 255u) != 0u) return false;
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (t0 == 0) t0 = now;
+        return now - t0 > kWaitNs;
+    }
+};
 constexpr uint32_t kOld = 1u, kNew = 2u;
 
 // ---------------------------------------------------------------- float-float
@@ -146,6 +165,12 @@ struct AxisList {
 
 __device__ __forceinline__ int wrapc(int x, int T) { return x < 0 ? x + T : (x >= T ? x - T : x); }
 
+template <typename V>
+__device__ __forceinline__ V sel4(const V (&v)[4], int i)
+{
+    return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+
 // {p-1, p, p+1} flagged f0, united with {q-1, q, q+1} flagged kNew when cross
 __device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t f0, int T)
 {
@@ -188,13 +213,6 @@ __device__ __forceinline__ bool in_work(const Trial &t, int x, int y, int z, int
     return t.cross && near1(x - (int)t.qx, T) && near1(y - (int)t.qy, T) && near1(z - (int)t.qz, T);
 }
 
-// cells of one (y, z) row of a trial's neighbourhood: up to 4, flagged
-struct Row {
-    int cell[4];
-    uint32_t fl[4];
-    int p1, p2, p3, tot;
-};
-
 // ---------------------------------------------------------------- shared state
 struct WordRec {
     uint32_t w[8];
@@ -202,24 +220,35 @@ struct WordRec {
     int pad[3];
 };
 
-struct Slot {  // evaluator -> committer
-    Trial t;
-    uint4 last_val;
-    float hi, lo, uab;
-    int self_slot;
-    int c0;
-    int ready;  // move + 1 when filled
+constexpr int kGMax = 8;  // warps per evaluation team, at most
+
+struct Slot {  // evaluators -> committer, one per move in flight
+    Trial t;                      // written by the team's warp 0
+    uint4 last_val;               // the old cell's last entry (by the lane that met it)
+    float ph[kGMax], pu[kGMax];   // per-warp FP32 sums: dU, uabs
+    double pd[kGMax], pa[kGMax];  // per-warp FP64 sums: dU, uabs
+    int self_slot;                // the trial particle's slot in its old cell, -1 none
+    int has_last;
+    int c0;                       // moves committed when the evaluation started
+    int arrive;                   // warps finished
+    int tag;                      // move + 1 of the evaluation under way, 0 none
+    int pad[2];
 };
 
 struct LogRec {  // committer -> evaluation validity
-    int flags;   // bit0 accepted, bit1 N changed
-    int mx[3], my[3], mz[3];
-    int ids[3];  // (s << 24) | index of records written
+    int flags;         // bit0 accepted, bit1 N changed
+    int mx[3], my[3], mz[3];  // cells written (-1 none)
+    int cchg[3];       // 1: that cell's count changed (append or removal)
+    int ids[3];        // (s << 24) | index of records written
+    int np;            // positions that gained or lost a particle
+    uint4 pos[2];
 };
 
 struct BookRec {  // committer -> keeper
-    double dU, lnA;
+    double dU64, lnA;  // dU when decided in FP64 or evaluated in FP64 mode
+    float hi, lo;      // dU = hi + lo otherwise
     float uab;
+    int use64;
     int fin;      // bit0 accepted
     int type, sp, index;
     int possible;
@@ -244,7 +273,7 @@ struct __align__(16) Shared {
     int booked;     // moves the keeper has processed
     int stop;       // the committer stopped: no further moves are taken
     int status;
-    int dummy;
+    int where;      // which waits gave up: 1 team leader, 2 committer, 4 keeper
 };
 
 __device__ __forceinline__ int vload(const int &x) { return *(volatile const int *)&x; }
@@ -275,6 +304,23 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
         de += (double)sign * u;
         da += m;
     }
+}
+
+// The Metropolis test of Eqs. 3-5 (textbook sign of mu) in FP32 with an
+// explicit error band: 1 accept, 0 reject, -1 inside the band or not finite
+// (the caller decides in FP64).  ns: N_s before the move.
+__device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, int ns, float lnu, float dUf,
+                                          float uab)
+{
+    const float beta_f = (float)a.beta, tol_f = (float)a.tol;
+    float lnK = 0.f;
+    if (type == 1) lnK = a.lnzv_f[sp] - logf((float)(ns + 1));
+    else if (type == 2) lnK = logf((float)ns) - a.lnzv_f[sp];
+    const float lnA = lnK - beta_f * dUf;
+    const float band = beta_f * tol_f * uab + 1e-6f * (1.f + fabsf(lnK) + fabsf(beta_f * dUf) + fabsf(lnu));
+    const float diff = lnu - lnA;
+    if (fabsf(diff) > band) return (diff < 0.f) ? 1 : 0;
+    return -1;
 }
 
 // ---------------------------------------------------------------- the chain
@@ -381,82 +427,55 @@ struct Chain {
         return t;
     }
 
-    __device__ __forceinline__ int nrows(const Trial &t) const
+    // The cells a trial visits (its work list), indexed 0 .. nwork - 1: the
+    // 27 around its primary cell (no cell change, insertions, deletions);
+    // for a displacement into an adjacent cell the union of the old and new
+    // neighbourhoods, 3 or 4 values per axis, each cell flagged kOld and/or
+    // kNew (cells of the union box in neither neighbourhood carry no flag);
+    // for a longer displacement the old 27 (kOld) followed by the new 27
+    // (kNew).  At most 64 cells.
+    __device__ __forceinline__ int nwork(const Trial &t) const
     {
         if (!t.possible) return 0;
-        if (!t.cross) return 9;
-        if (t.far) return 18;
-        const int ny = (t.py == t.qy) ? 3 : (T == 3 ? 3 : 4);
-        const int nz = (t.pz == t.qz) ? 3 : (T == 3 ? 3 : 4);
-        return ny * nz;
+        if (!t.cross) return 27;
+        if (t.far) return 54;
+        const int nx = (t.px == t.qx || T == 3) ? 3 : 4;
+        const int ny = (t.py == t.qy || T == 3) ? 3 : 4;
+        const int nz = (t.pz == t.qz || T == 3) ? 3 : 4;
+        return nx * ny * nz;
     }
 
-    // Row r of the neighbourhood: a near cell-changing displacement visits
-    // the union of both neighbourhoods once (cells flagged old and/or new); a
-    // far one visits the old neighbourhood (rows 0-8) and the new (9-17).
-    __device__ __forceinline__ Row row(const Trial &t, int r) const
+    __device__ __forceinline__ void work_cell(const Trial &t, const AxisList &X, const AxisList &Y,
+                                              const AxisList &Z, int i, int &cell, uint32_t &fl) const
     {
-        Row R;
-        if (!t.cross) {  // the common case: 3 x 3 rows of 3 cells
-            const int iz = (r * 11) >> 5, iy = r - 3 * iz;  // r / 3 for r < 16
-            const int y = wrapc((int)t.py + iy - 1, T), z = wrapc((int)t.pz + iz - 1, T);
-            const int base = (z * T + y) * T;
-            R.cell[0] = base + wrapc((int)t.px - 1, T);
-            R.cell[1] = base + (int)t.px;
-            R.cell[2] = base + wrapc((int)t.px + 1, T);
-            R.cell[3] = 0;
-            R.fl[0] = R.fl[1] = R.fl[2] = t.fpri;
-            R.fl[3] = 0;
-            const int n0 = cnt[R.cell[0]], n1 = cnt[R.cell[1]], n2 = cnt[R.cell[2]];
-            R.p1 = n0;
-            R.p2 = n0 + n1;
-            R.p3 = R.p2 + n2;
-            R.tot = R.p3;
-            return R;
+        if (!t.cross || t.far) {
+            const bool nw = t.far && i >= 27;
+            const int k = nw ? i - 27 : i;
+            const int dz = k / 9, r = k - 9 * (k / 9);
+            const int dy = r / 3, dx = r - 3 * (r / 3);
+            const int cx = nw ? (int)t.qx : (int)t.px, cy = nw ? (int)t.qy : (int)t.py;
+            const int cz = nw ? (int)t.qz : (int)t.pz;
+            cell = (wrapc(cz + dz - 1, T) * T + wrapc(cy + dy - 1, T)) * T + wrapc(cx + dx - 1, T);
+            fl = t.far ? (nw ? kNew : kOld) : (uint32_t)t.fpri;
+            return;
         }
-        AxisList X, Y, Z;
-        if (t.far) {
-            const bool nw = r >= 9;
-            r = nw ? r - 9 : r;
-            const uint32_t fl = nw ? kNew : kOld;
-            X = axis_list(nw ? (int)t.qx : (int)t.px, 0, 0, fl, T);
-            Y = axis_list(nw ? (int)t.qy : (int)t.py, 0, 0, fl, T);
-            Z = axis_list(nw ? (int)t.qz : (int)t.pz, 0, 0, fl, T);
+        int ix, q1, iy, iz;
+        if (X.n == 4) {
+            ix = i & 3;
+            q1 = i >> 2;
         } else {
-            X = axis_list(t.px, t.qx, 1, kOld, T);
-            Y = axis_list(t.py, t.qy, 1, kOld, T);
-            Z = axis_list(t.pz, t.qz, 1, kOld, T);
+            q1 = i / 3;
+            ix = i - 3 * q1;
         }
-        const int iz = (Y.n == 4) ? (r >> 2) : ((r * 11) >> 5);
-        const int iy = r - iz * Y.n;
-        uint32_t fyz = 0;
-        int vy = 0, vz = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (j == iy) {
-                fyz = Y.f[j];
-                vy = Y.v[j];
-            }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (j == iz) {
-                fyz &= Z.f[j];
-                vz = Z.v[j];
-            }
-        const int base = (vz * T + vy) * T;
-        int n[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t f = (k < X.n) ? (X.f[k] & fyz) : 0u;
-            R.fl[k] = f;
-            R.cell[k] = base + X.v[k];
-            n[k] = f ? (int)cnt[R.cell[k]] : 0;
+        if (Y.n == 4) {
+            iy = q1 & 3;
+            iz = q1 >> 2;
+        } else {
+            iz = q1 / 3;
+            iy = q1 - 3 * iz;
         }
-        R.p1 = n[0];
-        R.p2 = R.p1 + n[1];
-        R.p3 = R.p2 + n[2];
-        R.tot = R.p3 + n[3];
-        return R;
+        cell = (sel4(Z.v, iz) * T + sel4(Y.v, iy)) * T + sel4(X.v, ix);
+        fl = sel4(X.f, ix) & sel4(Y.f, iy) & sel4(Z.f, iz);
     }
 
     // One item (a particle of a work cell) against the trial's old and/or new
@@ -512,112 +531,132 @@ struct Chain {
         }
     }
 
-    // Energy change of a trial over rows r0, r0 + rstep, ... of its
-    // neighbourhood (one warp).  P32: FP32 pair terms, plain FP32 sums per
-    // lane, float-float across lanes; else FP64 throughout.  Also finds the
-    // trial particle's slot and the old cell's last particle.
+    // One warp's share of a trial's energy change.  The items (particles) of
+    // the work cells are numbered in work-list order; warp j of a team of G
+    // takes the contiguous range [j P / G, (j + 1) P / G) of the P items, 32
+    // KU items per pass (KU per lane, loads in flight together).  P32: FP32
+    // pair terms summed in FP32 per lane and across the warp; else FP64.
+    // Returns the warp's sums (in every lane) and, in the lane that met
+    // them, the trial particle's slot in its old cell and that cell's last
+    // entry.
+    struct Part {
+        float e, ua;
+        double de, da;
+        int self_slot, has_last;
+        uint4 last;
+    };
+
     template <bool P32>
-    __device__ __forceinline__ void energy(const Trial &t, int r0, int rstep, FF &e, float &ua, double &de,
-                                           double &da, int &self_slot, uint4 &last_val, int &found_last) const
+    __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, float &acc,
+                                         float &mag, double &de, double &da) const
     {
-        e = FF{0.f, 0.f};
-        ua = 0.f;
-        de = da = 0.0;
+        if constexpr (P32) {
+            if (t.type == 0) item32<3>(t, q, valid, fl, acc, mag);
+            else if (t.type == 1) item32<2>(t, q, valid, fl, acc, mag);
+            else item32<1>(t, q, valid, fl, acc, mag);
+        } else if (valid && q.w != t.Po.w) {
+            FF e0 = {0.f, 0.f};
+            float u0 = 0.f;
+            const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
+            if (fl & kOld) pair_terms<false>(t.Po, q, a, kk, -1.f, e0, u0, de, da);
+            if (fl & kNew) pair_terms<false>(t.Pn, q, a, kk, 1.f, e0, u0, de, da);
+        }
+    }
+
+    template <bool P32, int KU>
+    __device__ __forceinline__ Part eval_part(const Trial &t, int j, int G) const
+    {
+        Part o;
+        o.self_slot = -1;
+        o.has_last = 0;
+        o.last = make_uint4(0, 0, 0, 0);
         float acc = 0.f, mag = 0.f;
-        int my_self = -1, my_last = 0;
-        uint4 my_lv = make_uint4(0, 0, 0, 0);
-        const int rows = nrows(t);
-        for (int r = r0; r < rows; r += 2 * rstep) {
-            const Row R0 = row(t, r);
-            Row R1;
-            R1.tot = 0;
-            if (r + rstep < rows) R1 = row(t, r + rstep);
-            // up to 4 loads (2 rows x 2 items per lane) in flight together
-            uint4 q[4];
-            int cl[4], sl[4];
-            uint32_t fl[4];
+        double de = 0.0, da = 0.0;
+        const int nw = nwork(t);
+        AxisList X, Y, Z;
+        X.n = Y.n = Z.n = 3;
+        if (t.cross && !t.far) {
+            X = axis_list(t.px, t.qx, 1, kOld, T);
+            Y = axis_list(t.py, t.qy, 1, kOld, T);
+            Z = axis_list(t.pz, t.qz, 1, kOld, T);
+        }
+        // a lane owns work cells lane and lane + 32
+        int ca = 0, cb = 0, na = 0, nb = 0;
+        uint32_t fa = 0, fb = 0;
+        if (lane < nw) {
+            work_cell(t, X, Y, Z, lane, ca, fa);
+            na = fa ? (int)cnt[ca] : 0;
+        }
+        if (lane + 32 < nw) {
+            work_cell(t, X, Y, Z, lane + 32, cb, fb);
+            nb = fb ? (int)cnt[cb] : 0;
+        }
+        // items end at ia (cells 0 .. 31) and ib (cells 32 .. 63), inclusive
+        const int ia = warp_inclusive_scan(na);
+        const int ib = warp_inclusive_scan(nb) + __shfl_sync(0xffffffffu, ia, 31);
+        const int P = __shfl_sync(0xffffffffu, ib, 31);
+        const int lo = (P * j) / G, hi = (P * (j + 1)) / G;
+        for (int base = lo; base < hi; base += 32 * KU) {
+            int cell[KU], slot[KU], ncl[KU];
+            uint32_t flg[KU];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const Row &R = (k < 2) ? R0 : R1;
-                const int f = lane + 32 * (k & 1);
-                cl[k] = -1;
-                sl[k] = 0;
-                fl[k] = 0;
-                q[k] = make_uint4(0, 0, 0, 0xFFFFFFFEu);
-                if (f < R.tot) {
-                    const int j = (f >= R.p1) + (f >= R.p2) + (f >= R.p3);
-                    const int b = j == 0 ? 0 : (j == 1 ? R.p1 : (j == 2 ? R.p2 : R.p3));
-                    cl[k] = j == 0 ? R.cell[0] : (j == 1 ? R.cell[1] : (j == 2 ? R.cell[2] : R.cell[3]));
-                    fl[k] = j == 0 ? R.fl[0] : (j == 1 ? R.fl[1] : (j == 2 ? R.fl[2] : R.fl[3]));
-                    sl[k] = f - b;
-                    q[k] = a.cell_pos[(long long)cl[k] * a.cap + sl[k]];
+            for (int u = 0; u < KU; ++u) {
+                cell[u] = -1;
+                slot[u] = 0;
+                ncl[u] = 0;
+                flg[u] = 0;
+            }
+            const int fend = min(hi, base + 32 * KU) - 1;
+            // the work cells holding items base .. fend (warp-uniform)
+            const int c0 = __popc(__ballot_sync(0xffffffffu, ia <= base)) + __popc(__ballot_sync(0xffffffffu, ib <= base));
+            const int c1 = __popc(__ballot_sync(0xffffffffu, ia <= fend)) + __popc(__ballot_sync(0xffffffffu, ib <= fend));
+            for (int c = c0; c <= c1; ++c) {
+                const int src = c & 31;
+                const bool up = c >= 32;
+                const int end = __shfl_sync(0xffffffffu, up ? ib : ia, src);
+                const int nc = __shfl_sync(0xffffffffu, up ? nb : na, src);
+                const int cid = __shfl_sync(0xffffffffu, up ? cb : ca, src);
+                const uint32_t fl = __shfl_sync(0xffffffffu, up ? fb : fa, src);
+                const int st = end - nc;
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    const int f = base + lane + 32 * u;
+                    if (f >= st && f < end && f < hi) {
+                        cell[u] = cid;
+                        slot[u] = f - st;
+                        ncl[u] = nc;
+                        flg[u] = fl;
+                    }
                 }
             }
+            uint4 q[KU];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (cl[k] == t.co && cl[k] >= 0) {
-                    if (q[k].w == t.Po.w) my_self = sl[k];
-                    else if (sl[k] == (int)cnt[cl[k]] - 1) {
-                        my_last = 1;
-                        my_lv = q[k];
+            for (int u = 0; u < KU; ++u)
+                q[u] = (cell[u] >= 0) ? a.cell_pos[(long long)cell[u] * a.cap + slot[u]]
+                                      : make_uint4(0, 0, 0, 0xFFFFFFFEu);
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const bool v = cell[u] >= 0;
+                if (v && (flg[u] & kOld) && cell[u] == t.co) {
+                    if (q[u].w == t.Po.w) o.self_slot = slot[u];
+                    else if (slot[u] == ncl[u] - 1) {
+                        o.has_last = 1;
+                        o.last = q[u];
                     }
                 }
-                if constexpr (P32) {
-                    if (t.type == 0) item32<3>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
-                    else if (t.type == 1) item32<2>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
-                    else item32<1>(t, q[k], cl[k] >= 0, fl[k], acc, mag);
-                } else if (cl[k] >= 0 && q[k].w != t.Po.w) {
-                    const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q[k].w);
-                    if (fl[k] & kOld) pair_terms<false>(t.Po, q[k], a, kk, -1.f, e, ua, de, da);
-                    if (fl[k] & kNew) pair_terms<false>(t.Pn, q[k], a, kk, 1.f, e, ua, de, da);
-                }
-            }
-            // dense rows: items beyond the first 64 of a row
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
-                const Row &R = k ? R1 : R0;
-                for (int f = 64 + lane; f < R.tot; f += 32) {
-                    const int j = (f >= R.p1) + (f >= R.p2) + (f >= R.p3);
-                    const int b = j == 0 ? 0 : (j == 1 ? R.p1 : (j == 2 ? R.p2 : R.p3));
-                    const int c = j == 0 ? R.cell[0] : (j == 1 ? R.cell[1] : (j == 2 ? R.cell[2] : R.cell[3]));
-                    const uint32_t g = j == 0 ? R.fl[0] : (j == 1 ? R.fl[1] : (j == 2 ? R.fl[2] : R.fl[3]));
-                    const int sl2 = f - b;
-                    const uint4 qq = a.cell_pos[(long long)c * a.cap + sl2];
-                    if (c == t.co) {
-                        if (qq.w == t.Po.w) my_self = sl2;
-                        else if (sl2 == (int)cnt[c] - 1) {
-                            my_last = 1;
-                            my_lv = qq;
-                        }
-                    }
-                    if constexpr (P32) {
-                        if (t.type == 0) item32<3>(t, qq, true, g, acc, mag);
-                        else if (t.type == 1) item32<2>(t, qq, true, g, acc, mag);
-                        else item32<1>(t, qq, true, g, acc, mag);
-                    } else if (qq.w != t.Po.w) {
-                        const int kk = (int)t.s * kMaxSpecies + (int)tag_species(qq.w);
-                        if (g & kOld) pair_terms<false>(t.Po, qq, a, kk, -1.f, e, ua, de, da);
-                        if (g & kNew) pair_terms<false>(t.Pn, qq, a, kk, 1.f, e, ua, de, da);
-                    }
-                }
+                item<P32>(t, q[u], v, flg[u], acc, mag, de, da);
             }
         }
         if constexpr (P32) {
-            e = FF{warp_sum(acc), 0.f};
-            ua = warp_sum(mag);
+            o.e = warp_sum(acc);
+            o.ua = warp_sum(mag);
+            o.de = o.da = 0.0;
         } else {
-            de = warp_sum(de);
-            da = warp_sum(da);
+            o.e = o.ua = 0.f;
+            o.de = warp_sum(de);
+            o.da = warp_sum(da);
         }
-        const unsigned bs = __ballot_sync(0xffffffffu, my_self >= 0);
-        self_slot = bs ? __shfl_sync(0xffffffffu, my_self, __ffs(bs) - 1) : -1;
-        const unsigned bl = __ballot_sync(0xffffffffu, my_last != 0);
-        found_last = bl ? 1 : 0;
-        const int src = bl ? __ffs(bl) - 1 : 0;
-        last_val.x = __shfl_sync(0xffffffffu, my_lv.x, src);
-        last_val.y = __shfl_sync(0xffffffffu, my_lv.y, src);
-        last_val.z = __shfl_sync(0xffffffffu, my_lv.z, src);
-        last_val.w = __shfl_sync(0xffffffffu, my_lv.w, src);
+        return o;
     }
 
     // the words of moves [m0, m0 + count) (count <= 32), computed by one warp
@@ -646,11 +685,12 @@ struct Chain {
         }
     }
 
-    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z) const
+    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z, int count_changed) const
     {
         L.mx[nm] = x;
         L.my[nm] = y;
         L.mz[nm] = z;
+        L.cchg[nm] = count_changed;
         ++nm;
     }
 
@@ -666,7 +706,7 @@ struct Chain {
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, t.Po.w);
                     if (!t.cross) {
                         a.cell_pos[(long long)t.co * a.cap + self_slot] = v;
-                        note(L, nm, t.px, t.py, t.pz);
+                        note(L, nm, t.px, t.py, t.pz, 0);
                     } else {
                         const int c_o = cnt[t.co];
                         if (self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
@@ -674,9 +714,12 @@ struct Chain {
                         const int c_n = cnt[t.cn];
                         a.cell_pos[(long long)t.cn * a.cap + c_n] = v;
                         cnt[t.cn] = (uint16_t)(c_n + 1);
-                        note(L, nm, t.px, t.py, t.pz);
-                        note(L, nm, t.qx, t.qy, t.qz);
+                        note(L, nm, t.px, t.py, t.pz, 1);
+                        note(L, nm, t.qx, t.qy, t.qz, 1);
                     }
+                    L.pos[0] = t.Po;
+                    L.pos[1] = t.Pn;
+                    L.np = 2;
                     a.pos_by_id[sb + t.idx] = v;
                     L.ids[nid++] = (sp << 24) | t.idx;
                 } else {
@@ -689,8 +732,10 @@ struct Chain {
                     sh.n[sp] = ni + 1;
                     sh.ln_n[sp] = logf((float)(ni + 1));
                     sh.ln_n1[sp] = logf((float)(ni + 2));
-                    note(L, nm, t.qx, t.qy, t.qz);
+                    note(L, nm, t.qx, t.qy, t.qz, 1);
                     L.ids[nid++] = (sp << 24) | (int)ni;
+                    L.pos[0] = t.Pn;
+                    L.np = 1;
                 }
                 for (int q = nm; q < 3; ++q) L.mx[q] = -1;
                 for (int q = nid; q < 3; ++q) L.ids[q] = -1;
@@ -701,9 +746,11 @@ struct Chain {
         // deletion: swap-with-last inside the cell, then the species' last
         // index takes the freed index (its record and its cell entry)
         const long long last = sh.n[sp] - 1;
+        int swapped = 0;
         if (lane == 0) {
             const int c_o = cnt[t.co];
-            if (self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
+            swapped = self_slot != c_o - 1;
+            if (swapped) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
             cnt[t.co] = (uint16_t)(c_o - 1);
         }
         __syncwarp();
@@ -727,10 +774,12 @@ struct Chain {
             if (lane == 0) a.pos_by_id[sb + t.idx] = make_uint4(Q.x, Q.y, Q.z, ntag);
         }
         if (lane == 0) {
-            note(L, nm, t.px, t.py, t.pz);
+            note(L, nm, t.px, t.py, t.pz, 1);
+            L.pos[0] = t.Po;
+            L.np = 1;
             L.ids[nid++] = (sp << 24) | t.idx;
             if (qx >= 0) {
-                note(L, nm, qx, qy, qz);
+                note(L, nm, qx, qy, qz, 0);
                 L.ids[nid++] = (sp << 24) | (int)last;
             }
             for (int q = nm; q < 3; ++q) L.mx[q] = -1;
@@ -743,6 +792,27 @@ struct Chain {
     }
 };
 
+// Whether some point of the grid box spanned by X0 and X1 (per axis, in
+// minimum-image coordinates relative to P) lies within the cutoff of P.
+// A record overwritten in place may be read with coordinates from either
+// value, so a move's old and new positions are tested as a box.
+__device__ __forceinline__ long long axis_gap(uint32_t a0, uint32_t a1, uint32_t p)
+{
+    long long lo = (int)(a0 - p), hi = (int)(a1 - p);
+    if (lo > hi) {
+        const long long t = lo;
+        lo = hi;
+        hi = t;
+    }
+    return lo > 0 ? lo : (hi < 0 ? -hi : 0);
+}
+
+__device__ __forceinline__ bool box_within(const uint4 &X0, const uint4 &X1, const uint4 &P, unsigned long long R2)
+{
+    const long long dx = axis_gap(X0.x, X1.x, P.x), dy = axis_gap(X0.y, X1.y, P.y), dz = axis_gap(X0.z, X1.z, P.z);
+    return (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy) + (unsigned long long)(dz * dz) < R2;
+}
+
 // Whether a move evaluated after `c0` commits is still valid after `m`: no
 // committed move in [c0, m) touched its cells or wrote its particle's record,
 // and the current particle counts pick the same particle (or, for a move
@@ -753,6 +823,7 @@ __device__ __forceinline__ bool still_valid(const Chain<F32> &C, const Shared &s
 {
     bool bad = false;
     bool nchanged = false;
+    const ChainArgs &a = C.a;
     for (int j = c0 + lane; j < m; j += 32) {
         const LogRec &L = sh.logs[j % kRS];
         const int f = L.flags;
@@ -760,8 +831,24 @@ __device__ __forceinline__ bool still_valid(const Chain<F32> &C, const Shared &s
         if (f & 2) nchanged = true;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if (L.mx[q] >= 0 && in_work(t, L.mx[q], L.my[q], L.mz[q], T)) bad = true;
+            if (L.mx[q] >= 0) {
+                // the old cell's slots (self, last entry) must be as seen;
+                // a work cell whose count changed may have been seen with
+                // either count by the team's warps (their item ranges follow
+                // the counts)
+                const int c = (L.mz[q] * T + L.my[q]) * T + L.mx[q];
+                if (t.possible && t.type != 1 && c == t.co) bad = true;
+                if (L.cchg[q] && in_work(t, L.mx[q], L.my[q], L.mz[q], T)) bad = true;
+            }
             if (t.possible && t.type != 1 && L.ids[q] >= 0 && L.ids[q] == (((int)t.s << 24) | t.idx)) bad = true;
+        }
+        // a particle that appeared, vanished or moved within rc of the
+        // trial's old or new position changes dU (exact integer cutoff, as
+        // in Eq. 1's sum)
+        if (t.possible) {
+            const uint4 X0 = L.pos[0], X1 = (L.np == 2) ? L.pos[1] : L.pos[0];
+            if (t.type != 1 && box_within(X0, X1, t.Po, a.R2)) bad = true;
+            if (t.type != 2 && box_within(X0, X1, t.Pn, a.R2)) bad = true;
         }
     }
     if (__any_sync(0xffffffffu, bad)) return false;
@@ -799,35 +886,29 @@ __device__ __forceinline__ void team_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Per-team hand-off area: the leader's decision for the team and the
-// warps' partial sums.
-template <int G>
-struct TeamShared {
-    Trial t;  // the trial, computed once by the leader warp
-    int go;   // 1 evaluate move m, 2 finished
-    int m;
-    int c0;
-    int pad;
-    float hi[G], lo[G], ua[G];
-    int self[G];
-    int has_last[G];
-    uint4 last[G];
+// Per-team hand-off area, double-buffered by iteration parity: the
+// leader's choice of move and the particle counts its evaluation uses.
+struct TeamCtl {
+    int go[2], m[2], c0[2], pad[2];
+    int ns[2][kMaxSpecies];
 };
 
 // NTEAM teams of G evaluator warps (warps 1 .. G * NTEAM), the committer
-// (warp 0) and the keeper (last warp).  Each team evaluates every
-// NTEAM-th move, its rows spread over the team's warps; a team has at most
-// one uncommitted move, so a move is evaluated at most NTEAM - 1 commits
-// ahead of its turn.
-template <bool F32, int G, int NTEAM>
+// (warp 0) and the keeper (last warp).  Team k evaluates moves k, k + NTEAM,
+// k + 2 NTEAM, ..., each as soon as fewer than LOOK moves separate it from
+// the committer; a move the committer finds invalid goes back to its team,
+// ahead of the team's new moves.  KU: slots per work cell a lane loads at
+// once.
+template <bool F32, int G, int NTEAM, int LOOK, int KU>
 __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
+    static_assert(G <= kGMax && LOOK < kRS && NTEAM <= 15, "team shape");
     constexpr int EW = G * NTEAM;
     constexpr int NTH = (EW + 2) * 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     uint16_t *cnt = (uint16_t *)dyn;
     __shared__ Shared sh;
-    __shared__ TeamShared<G> ts[NTEAM];
+    __shared__ TeamCtl ctl[NTEAM];
     __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
     // this CTA's chain: its arguments copied to shared memory
     __shared__ __align__(16) ChainArgs a;
@@ -861,7 +942,8 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.ns_ring[0][tid] = (int)v;
     }
     for (int k = tid; k < kRS; k += NTH) {
-        sh.slots[k].ready = 0;
+        sh.slots[k].tag = 0;
+        sh.slots[k].arrive = 0;
         sh.book[k].ready = 0;
         sh.logs[k].flags = 0;
     }
@@ -871,6 +953,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.booked = 0;
         sh.stop = 0;
         sh.status = 0;
+        sh.where = 0;
     }
     {
         const int first_fill = min(n, kRW);
@@ -883,119 +966,99 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
     if (warp >= 1 && warp <= EW) {
         // ------------------------------------------------------------ evaluators
         const int team = (warp - 1) / G, j = (warp - 1) % G;
-        TeamShared<G> &tsh = ts[team];
+        TeamCtl &tc = ctl[team];
         int next = team;  // the team's next new move (leader lane 0)
-        for (;;) {
+        for (int it = 0;; ++it) {
+            const int p = it & 1;
             if (j == 0 && lane == 0) {
-                long long spins = 0;
+                Wait wt;
+                int go = 0, mm = 0, c0 = 0;
                 for (;;) {
-                    const int com = vload(sh.committed);
                     if (vload(sh.stop)) {
-                        tsh.go = 2;
+                        go = 2;
                         break;
                     }
+                    const int com = vload(sh.committed);
                     const int rd = vload(redo[team]);
-                    if (rd) {
-                        vstore(redo[team], 0);
-                        tsh.m = rd - 1;
-                        tsh.c0 = com;
-                        tsh.go = 1;
-                        break;
-                    }
-                    if (next < n && next <= com + NTEAM && next < vload(sh.filled)) {
-                        tsh.m = next;
-                        tsh.c0 = com;
-                        tsh.go = 1;
-                        next += NTEAM;
-                        break;
+                    const bool fresh = next < n && next < com + LOOK && next < vload(sh.filled);
+                    if (rd || fresh) {
+                        // the counts after `com` commits (the ring entry stays
+                        // until com + kRS - 1 moves are committed)
+                        for (int q = 0; q < a.S; ++q) tc.ns[p][q] = sh.ns_ring[com % kRS][q];
+                        __threadfence_block();
+                        if (vload(sh.committed) < com + kRS - 1) {
+                            c0 = com;
+                            go = 1;
+                            if (rd) {
+                                vstore(redo[team], 0);
+                                mm = rd - 1;
+                            } else {
+                                mm = next;
+                                next += NTEAM;
+                            }
+                            break;
+                        }
+                        continue;
                     }
                     if (next >= n && com >= n) {
-                        tsh.go = 2;
+                        go = 2;
                         break;
                     }
-                    if (++spins > kSpinMax) {
+                    if (wt.expired()) {
                         atomicOr(&sh.status, kStatusTimeout);
+                        atomicOr(&sh.where, 1);
                         vstore(sh.stop, 1);
-                        tsh.go = 2;
+                        go = 2;
                         break;
                     }
                     __nanosleep(16);
                 }
-                __threadfence_block();
-            }
-            if (j == 0) {
-                __syncwarp();
-                if (tsh.go == 1) {
-                    const Trial tt = C.make_trial(tsh.m, sh.ns_ring[tsh.c0 % kRS]);
-                    if (lane == 0) tsh.t = tt;
-                }
-            }
-            team_sync(1 + team, G * 32);
-            const int go = tsh.go, m = tsh.m, c0 = tsh.c0;
-            if (go == 2) break;
-            const Trial t = tsh.t;
-            FF e;
-            float ua;
-            double de, da;
-            int self_slot, found_last;
-            uint4 last_val;
-            C.template energy<F32>(t, j, G, e, ua, de, da, self_slot, last_val, found_last);
-            if constexpr (!F32) {
-                e.hi = __double2float_rn(de);
-                e.lo = __double2float_rn(de - (double)e.hi);
-                ua = (float)da;
-            }
-            if (lane == 0) {
-                tsh.hi[j] = e.hi;
-                tsh.lo[j] = e.lo;
-                tsh.ua[j] = ua;
-                tsh.self[j] = self_slot;
-                tsh.has_last[j] = found_last;
-                tsh.last[j] = last_val;
-            }
-            team_sync(1 + team, G * 32);
-            if (j == 0) {
-                FF tot = {0.f, 0.f};
-                float uab = 0.f;
-                int self = -1, hl = 0;
-                uint4 lv = make_uint4(0, 0, 0, 0);
-                if (lane < G) {
-                    tot.hi = tsh.hi[lane];
-                    tot.lo = tsh.lo[lane];
-                    uab = tsh.ua[lane];
-                    self = tsh.self[lane];
-                    hl = tsh.has_last[lane];
-                    lv = tsh.last[lane];
-                }
-                tot = ff_warp_sum(tot);
-                uab = warp_sum(uab);
-                const unsigned bs = __ballot_sync(0xffffffffu, self >= 0);
-                const unsigned bl = __ballot_sync(0xffffffffu, hl != 0);
-                const int src_s = bs ? __ffs(bs) - 1 : 0, src_l = bl ? __ffs(bl) - 1 : 0;
-                const int self_all = bs ? __shfl_sync(0xffffffffu, self, src_s) : -1;
-                uint4 lv_all;
-                lv_all.x = __shfl_sync(0xffffffffu, lv.x, src_l);
-                lv_all.y = __shfl_sync(0xffffffffu, lv.y, src_l);
-                lv_all.z = __shfl_sync(0xffffffffu, lv.z, src_l);
-                lv_all.w = __shfl_sync(0xffffffffu, lv.w, src_l);
-                if (lane == 0) {
-                    Slot &S = sh.slots[m % kRS];
-                    S.t = t;
-                    S.last_val = lv_all;
-                    S.hi = tot.hi;
-                    S.lo = tot.lo;
-                    S.uab = uab;
-                    S.self_slot = self_all;
+                if (go == 1) {
+                    Slot &S = sh.slots[mm % kRS];
+                    S.self_slot = -1;
+                    S.has_last = 0;
+                    S.arrive = 0;
                     S.c0 = c0;
                     __threadfence_block();
-                    vstore(S.ready, m + 1);
+                    vstore(S.tag, mm + 1);
                 }
-                __syncwarp();
+                tc.go[p] = go;
+                tc.m[p] = mm;
+                tc.c0[p] = c0;
+                __threadfence_block();
+            }
+            // the whole leader warp reaches the team barrier together: the
+            // barrier counts warps, not lanes
+            __syncwarp();
+            team_sync(1 + team, G * 32);
+            if (tc.go[p] == 2) break;
+            const int m = tc.m[p];
+            const Trial t = C.make_trial(m, tc.ns[p]);
+            Slot &S = sh.slots[m % kRS];
+            const typename Chain<F32>::Part P = C.template eval_part<F32, KU>(t, j, G);
+            if (P.self_slot >= 0) S.self_slot = P.self_slot;
+            if (P.has_last) {
+                S.last_val = P.last;
+                S.has_last = 1;
+            }
+            if (lane == 0) {
+                if (j == 0) S.t = t;
+                if constexpr (F32) {
+                    S.ph[j] = P.e;
+                    S.pu[j] = P.ua;
+                } else {
+                    S.pd[j] = P.de;
+                    S.pa[j] = P.da;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicAdd(&S.arrive, 1);
             }
         }
     } else if (warp == 0) {
         // ------------------------------------------------------------ committer
-        const float beta_f = (float)a.beta, tol_f = (float)a.tol;
         for (int m = 0; m < n; ++m) {
             Slot &S = sh.slots[m % kRS];
             const int team = m % NTEAM;
@@ -1003,18 +1066,21 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             int c0 = 0, attempt = 0;
             for (;; ++attempt) {
                 // wait for the evaluation of m and for room in the keeper's book
-                long long spins = 0;
+                Wait wt;
                 for (;;) {
-                    int r = 0, bk = 0;
+                    int r = 0;
                     if (lane == 0) {
-                        r = vload(S.ready);
-                        bk = vload(sh.booked);
+                        const int tg = vload(S.tag);
+                        __threadfence_block();
+                        r = tg == m + 1 && vload(S.arrive) == G && m < vload(sh.booked) + kRS;
                     }
                     r = __shfl_sync(0xffffffffu, r, 0);
-                    bk = __shfl_sync(0xffffffffu, bk, 0);
-                    if (r == m + 1 && m < bk + kRS) break;
-                    if (++spins > kSpinMax) {
-                        if (lane == 0) atomicOr(&sh.status, kStatusTimeout);
+                    if (r) break;
+                    if (wt.expired()) {
+                        if (lane == 0) {
+                            atomicOr(&sh.status, kStatusTimeout);
+                            atomicOr(&sh.where, 2);
+                        }
                         ok = false;
                         break;
                     }
@@ -1025,7 +1091,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 if (c0 == m || still_valid<F32>(C, sh, S.t, c0, m, T, lane)) break;
                 // evaluate again against the configuration after m moves
                 if (lane == 0) {
-                    vstore(S.ready, 0);
+                    vstore(S.tag, 0);
                     __threadfence_block();
                     vstore(redo[team], m + 1);
                 }
@@ -1033,38 +1099,55 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             }
             if (!ok) break;
             const Trial t = S.t;
-            FF e = {S.hi, S.lo};
-            float uab = S.uab;
             const int self_slot = S.self_slot;
             const uint4 last_val = S.last_val;
+            // the team's partial sums in a fixed order (lanes >= G add zeros);
+            // lanes 0 .. 7 hold the totals and every lane takes lane 0's, so
+            // the whole warp decides alike
+            FF e = {0.f, 0.f};
+            float uab = 0.f;
+            double de = 0.0, da = 0.0;
+            if constexpr (F32) {
+                FF v = {lane < G ? S.ph[lane] : 0.f, 0.f};
+                float u = lane < G ? S.pu[lane] : 0.f;
+#pragma unroll
+                for (int o = kGMax / 2; o > 0; o >>= 1) {
+                    FF w;
+                    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+                    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+                    v = ff_add(v, w);
+                    u += __shfl_xor_sync(0xffffffffu, u, o);
+                }
+                e.hi = __shfl_sync(0xffffffffu, v.hi, 0);
+                e.lo = __shfl_sync(0xffffffffu, v.lo, 0);
+                uab = __shfl_sync(0xffffffffu, u, 0);
+            } else {
+                double v = lane < G ? S.pd[lane] : 0.0, u = lane < G ? S.pa[lane] : 0.0;
+#pragma unroll
+                for (int o = kGMax / 2; o > 0; o >>= 1) {
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                    u += __shfl_xor_sync(0xffffffffu, u, o);
+                }
+                de = __shfl_sync(0xffffffffu, v, 0);
+                da = __shfl_sync(0xffffffffu, u, 0);
+                e.hi = __double2float_rn(de);
+                uab = __double2float_rn(da);
+            }
             int refined = attempt > 0 ? 4 : 0;
             const int type = t.type, sp = t.s;
             const long long ns = sh.n[sp];
-            // Metropolis test in FP32 with an error band
-            int fin = 0;
-            double dU = (double)e.hi + (double)e.lo, lnA_d = 0.0;
-            bool decided = true;
-            if (t.possible) {
-                const float lnu = C.words(m).lnu;
-                float lnK = 0.f;
-                if (type == 1) lnK = a.lnzv_f[sp] - sh.ln_n1[sp];
-                else if (type == 2) lnK = sh.ln_n[sp] - a.lnzv_f[sp];
-                const float dUf = e.hi + e.lo;
-                const float lnA = lnK - beta_f * dUf;
-                const float band =
-                    beta_f * tol_f * uab + 1e-6f * (1.f + fabsf(lnK) + fabsf(beta_f * dUf) + fabsf(lnu));
-                const float diff = lnu - lnA;
-                if (fabsf(diff) > band) fin = (diff < 0.f) ? 1 : 0;
-                else decided = false;  // near the threshold, or not finite
-            }
-            if (!decided) {
-                // the whole trial in FP64: pair terms, sums, log
-                FF e2;
-                float u2;
-                double de, da;
-                int s2, f2;
-                uint4 l2;
-                C.template energy<false>(t, 0, 1, e2, u2, de, da, s2, l2, f2);
+            // the Metropolis test in FP32 with an error band
+            const int dec = t.possible ? decide_f32(a, type, sp, (int)ns, C.words(m).lnu, e.hi + e.lo, uab) : 0;
+            int fin = dec == 1 ? 1 : 0, use64 = F32 ? 0 : 1;
+            double lnA_d = 0.0;
+            if (dec < 0) {
+                // decide in FP64: in FP32 mode the whole trial is evaluated
+                // again in FP64 (pair terms and sums)
+                if constexpr (F32) {
+                    const typename Chain<F32>::Part Q = C.template eval_part<false, 4>(t, 0, 1);
+                    de = Q.de;
+                    da = Q.da;
+                }
                 const WordRec &W = C.words(m);
                 const double lnu = log(uniform53(W.w[6], W.w[7]));
                 double lnK = 0.0;
@@ -1074,7 +1157,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 fin = (lnu < lnA_d) ? 1 : 0;
                 const double band = a.beta * a.tol * da + 1e-12 * (1.0 + fabs(lnA_d));
                 refined |= 2 | ((fabs(lnu - lnA_d) <= band) ? 1 : 0);
-                dU = de;
+                use64 = 1;
                 uab = (float)da;
             }
             int stop_bits = 0;
@@ -1097,7 +1180,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             __syncwarp();
             if (lane == 0) {
                 BookRec &B = sh.book[m % kRS];
-                B.dU = dU;
+                B.dU64 = de;
+                B.hi = e.hi;
+                B.lo = e.lo;
+                B.use64 = use64;
                 B.lnA = lnA_d;
                 B.uab = uab;
                 B.fin = fin;
@@ -1121,7 +1207,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         long long flagged = 0, reeval = 0, refines = 0, Ncur = 0;
         for (int q = 0; q < kMaxSpecies; ++q) Ncur += sh.n[q];
         int mb = 0;
-        long long spins = 0;
+        Wait wt;
         for (;;) {
             // refill the words ring ahead of the evaluators
             int c = 0, f = 0, sp0 = 0;
@@ -1160,19 +1246,20 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                         acc0 += type == 0;
                         acc1 += type == 1;
                         acc2 += type == 2;
-                        E += B.dU;
+                        E += B.use64 ? B.dU64 : (double)B.hi + (double)B.lo;
                         Ncur += (type == 1) - (type == 2);
                     }
                     if (a.trace) {
+                        const double dU = B.use64 ? B.dU64 : (double)B.hi + (double)B.lo;
                         gcmc_trace tr;
                         double lnA = B.lnA;
                         if (!(B.refined & 2)) {
                             double lnK = 0.0;
                             if (type == 1) lnK = a.logz[B.sp] + a.lnV - log((double)(B.ns + 1));
                             else if (type == 2 && B.ns > 0) lnK = log((double)B.ns) - a.logz[B.sp] - a.lnV;
-                            lnA = B.possible ? lnK - a.beta * B.dU : -INFINITY;
+                            lnA = B.possible ? lnK - a.beta * dU : -INFINITY;
                         }
-                        tr.dU = B.possible ? B.dU : 0.0;
+                        tr.dU = B.possible ? dU : 0.0;
                         tr.lnA = lnA;
                         tr.uabs = B.possible ? (double)B.uab : 0.0;
                         tr.index = B.index;
@@ -1188,7 +1275,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 }
                 __syncwarp();
                 ++mb;
-                spins = 0;
+                wt = Wait();
                 continue;
             }
             if (mb >= n) break;
@@ -1200,9 +1287,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             stop = __shfl_sync(0xffffffffu, stop, 0);
             com = __shfl_sync(0xffffffffu, com, 0);
             if (stop && mb >= com) break;
-            if (++spins > kSpinMax) {
+            if (wt.expired()) {
                 if (lane == 0) {
                     atomicOr(&sh.status, kStatusTimeout);
+                    atomicOr(&sh.where, 4);
                     vstore(sh.stop, 1);
                 }
                 break;
@@ -1236,6 +1324,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         int st = sh.status;
         if (!(o.energy - o.energy == 0.0)) st |= kStatusNonFinite;
         o.status = st;
+        o.pad = sh.where;
     }
 }
 
@@ -1244,17 +1333,17 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
 // evaluate more moves ahead (better when moves rarely conflict); larger
 // teams evaluate one move faster (better when N changes often).
 constexpr int kNumConfigs = 4;
-static const int kConfigG[kNumConfigs] = {7, 3, 2, 1};
-static const int kConfigT[kNumConfigs] = {2, 2, 2, 3};
+static const int kConfigG[kNumConfigs] = {7, 4, 3, 2};
+static const int kConfigT[kNumConfigs] = {2, 3, 4, 6};
 
 template <bool F32>
 static void *chain_kernel(int config)
 {
     switch (config) {
-    case 1: return (void *)k_chain<F32, 3, 2>;
-    case 2: return (void *)k_chain<F32, 2, 2>;
-    case 3: return (void *)k_chain<F32, 1, 3>;
-    default: return (void *)k_chain<F32, 7, 2>;
+    case 1: return (void *)k_chain<F32, 4, 3, 6, 2>;
+    case 2: return (void *)k_chain<F32, 3, 4, 8, 2>;
+    case 3: return (void *)k_chain<F32, 2, 6, 12, 3>;
+    default: return (void *)k_chain<F32, 7, 2, 4, 2>;
     }
 }
 
@@ -1483,7 +1572,9 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
             j.done += o.moves_done;
             if (o.status & kStatusNonFinite) j.result = GCMC_ERR_NONFINITE;
             if (o.status & kStatusTimeout) {
-                j.result = fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_run_moves: a bounded wait inside the chain kernel gave up");
+                j.result = fail(ctx, GCMC_ERR_TIMEOUT,
+                                "gcmc_run_moves: a bounded wait inside the chain kernel gave up (sites " +
+                                    std::to_string(o.pad) + ")");
                 continue;
             }
             if (o.status & (kStatusCellOverflow | kStatusCapacity)) {

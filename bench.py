@@ -62,6 +62,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the throughput kernels (trial energies, total energy, gradient, cell build)")
     ap.add_argument("--cpu-moves", type=int, default=0, help="oracle moves per chain in the CPU sample")
     ap.add_argument("--cpu-workers", type=int, default=0)
     a = ap.parse_args()
@@ -401,25 +403,29 @@ def _kernel_figures(dev, flush, sm_mhz):
     ms_trial = ev_time(lambda: b.trial_energy_raw(tpd, tsd, tout))
     ms_total = ev_time(lambda: b.total_energy())
 
-    # FLOP model: 6 per candidate (separation, squared distance, cutoff) +
-    # 11 per pair within rc (1/r^2, s^6, s^12 - s^6, 4 eps, sums)
-    def alu(points, ms):
-        fl = points * (6.0 * cand + 11.0 * inr)
-        ach = fl / (ms / 1e3) / 1e12
+    # algorithmic work: pairs within the cutoff only (the other candidates of
+    # the 27 cells are overhead), 20 FLOP per pair forward, 30 backward
+    def alu(pairs, flop_per_pair, ms):
+        ach = pairs * flop_per_pair / (ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "flop_model": "6 per candidate + 11 per pair within rc"}
+                "traffic": None, "flop_model": "%d per pair within rc" % flop_per_pair,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock"}
 
     out["trial_energy_mixture_1m"] = {"points": m, "ms": ms_trial, "points_per_s": m / (ms_trial / 1e3),
                                       "candidates_per_point": cand, "pairs_in_rc_per_point": inr,
-                                      "roofline": alu(m, ms_trial)}
-    out["total_energy_mixture_1m"] = {"particles": N, "ms": ms_total, "roofline": alu(N, ms_total)}
+                                      "roofline": alu(m * inr, 20, ms_trial)}
+    out["total_energy_mixture_1m"] = {"particles": N, "ms": ms_total, "unique_pairs_in_rc": N * inr / 2,
+                                      "roofline": alu(N * inr / 2, 20, ms_total)}
     out["cell_build_mixture_1m"] = {"particles": N, "ms": ms_build, "particles_per_s": N / (ms_build / 1e3)}
     del b, tpd, tsd, tout
     w5 = W.c5_gradient()
     b5 = Box(w5.L, w5.rc, w5.eps, w5.sigma, precision="fp32", device=dev)
     b5.build_cells(torch.from_numpy(w5.positions()).to(dev), torch.from_numpy(w5.types()).to(dev))
     ms_grad = ev_time(lambda: b5.energy_grad(want_pos=True))
-    out["energy_grad_262k"] = {"particles": w5.n, "ms": ms_grad, "particles_per_s": w5.n / (ms_grad / 1e3)}
+    inr5 = 4.0 / 3.0 * math.pi * w5.rc ** 3 * (w5.n / w5.L ** 3)
+    out["energy_grad_262k"] = {"particles": w5.n, "ms": ms_grad, "particles_per_s": w5.n / (ms_grad / 1e3),
+                               "unique_pairs_in_rc": w5.n * inr5 / 2,
+                               "roofline": alu(w5.n * inr5 / 2, 30, ms_grad)}
     return out
 
 
@@ -437,6 +443,12 @@ def main():
 
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.kernels_only:
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        print(json.dumps({"kernels": _kernel_figures(dev, flush, None)}))
+        return 0
     chains = _chains(a.workload)
     # the CPU baseline's worker processes are spawned before the first GPU call
     pool = None

@@ -46,6 +46,10 @@ if ROOT not in sys.path:
 METRIC = "GCMC moves/sec at 1 GB300 (FP32+batched vs plain FP64) at ΔE rel err ≤1e-5"
 UNIT = "moves/s"
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one full-size chain launch (64 chains x 10^5
+# moves) from an ncu capture (profiles/k_chain_isotherm_fp32.md), valid for
+# the chain kernel source with this sha256 prefix only
+CHAIN_TRAFFIC = {"sha256_prefix": "1c00edae4f88bceb", "bytes": 22.87e6, "moves": 6.4e6}
 DEFAULT_MOVES = {"isotherm": 100_000, "c2": 1_000_000, "c1": 10_000}
 DEFAULT_CPU_MOVES = {"isotherm": 20_000, "c2": 1_000_000, "c1": 10_000}
 
@@ -509,8 +513,16 @@ def main():
     chain_ms = sum(chain_times) / len(chain_times)
     achieved = K * M / (chain_ms / 1e3)
     peak = K * 1e9 / probe.floor_ns if rc == 0 and probe.floor_ns > 0 else None
+    traffic = None
+    try:
+        import hashlib
+        src = os.path.join(ROOT, "paper_1408_3764_gb300", "csrc", "gcmc_chain.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(CHAIN_TRAFFIC["sha256_prefix"]):
+            traffic = CHAIN_TRAFFIC["bytes"] * (K * M) / CHAIN_TRAFFIC["moves"]
+    except OSError:
+        pass
     roofline = {"bound": "latency", "achieved": achieved, "peak": peak, "unit": UNIT,
-                "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": "k_chain",
+                "frac": (achieved / peak) if peak else None, "traffic": traffic, "kernel": "k_chain",
                 "launch_ms": chain_ms,
                 "floor_ns_per_move": probe.floor_ns,
                 "context_ns": {"l2_hop": probe.l2_hop_ns, "cta_reduction": probe.sync_round_ns,

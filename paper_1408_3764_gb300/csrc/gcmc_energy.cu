@@ -4,8 +4,8 @@
 //   k_cell_energy    full-system energy, one CTA per home cell (the
 //                    cell-list CalculateTotalEnergy of Sec. 3.1.1);
 //   k_cell_grad      its hand-written gradient (positions, eps, sigma, virial).
-// FP32 mode: pair terms in FP32, per-lane sums compensated (Neumaier), lane
-// and block sums in FP64.  FP64 mode: everything in FP64.
+// FP32 mode: pair terms and per-lane sums in FP32, sums across cells in
+// FP64.  FP64 mode: everything in FP64.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -15,30 +15,21 @@
 
 namespace gcmc {
 
-// Neumaier-compensated float accumulator.
-struct CSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float t = s + x;
-        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
+// Per-lane accumulators.  FP32 mode: plain FP32 sums (a lane adds a few
+// dozen terms, so their rounding stays near 1e-6 of the terms' magnitudes);
+// FP64 mode: FP64.
 template <bool F32>
 struct Acc;
 template <>
 struct Acc<true> {
-    CSum e, a;
+    float e = 0.f, a = 0.f;
     __device__ __forceinline__ void add(float u, float m)
     {
-        e.add(u);
-        a.add(m);
+        e += u;
+        a += m;
     }
-    __device__ __forceinline__ double ev() const { return e.value(); }
-    __device__ __forceinline__ double av() const { return a.value(); }
+    __device__ __forceinline__ double ev() const { return (double)e; }
+    __device__ __forceinline__ double av() const { return (double)a; }
 };
 template <>
 struct Acc<false> {
@@ -143,11 +134,15 @@ __global__ void __launch_bounds__(256) k_trial_energy(
     Runs &R = runs[w];
     const int64_t warps = (int64_t)gridDim.x * 8;
     for (int64_t k = (int64_t)blockIdx.x * 8 + w; k < m; k += warps) {
+        // lanes 0, 1, 2 quantise x, y, z (FP64 work on three lanes only)
         bool ok = true;
+        uint32_t Xl = 0u;
+        if (lane < 3) Xl = quantize_dev(pos[3 * k + lane], q, ok);
+        ok = __all_sync(0xffffffffu, ok);
         uint4 P;
-        P.x = quantize_dev(pos[3 * k + 0], q, ok);
-        P.y = quantize_dev(pos[3 * k + 1], q, ok);
-        P.z = quantize_dev(pos[3 * k + 2], q, ok);
+        P.x = __shfl_sync(0xffffffffu, Xl, 0);
+        P.y = __shfl_sync(0xffffffffu, Xl, 1);
+        P.z = __shfl_sync(0xffffffffu, Xl, 2);
         const int t = species[k];
         uint32_t excl = 0xFFFFFFFFu;
         if (exclude) {
@@ -172,8 +167,14 @@ __global__ void __launch_bounds__(256) k_trial_energy(
             const uint4 qv = cpos[idx];
             pair_acc<F32>(P, qv, excl, R2, t, ff, fd, acc);
         }
-        const double e = warp_sum(acc.ev());
-        const double a = warp_sum(acc.av());
+        double e, a;
+        if constexpr (F32) {
+            e = (double)warp_sum(acc.e);
+            a = (double)warp_sum(acc.a);
+        } else {
+            e = warp_sum(acc.ev());
+            a = warp_sum(acc.av());
+        }
         if (lane == 0) {
             out[k] = e;
             if (out_abs) out_abs[k] = a;
@@ -183,9 +184,12 @@ __global__ void __launch_bounds__(256) k_trial_energy(
 }
 
 // ---------------------------------------------------------------------------
-// Full-system energy: one CTA per home cell; the 27 neighbour cells are
-// staged in shared memory, each warp takes home particles, lanes take the
-// staged partners.  Pairs are visited from both sides; the host halves.
+// Full-system energy: one CTA per home cell.  Each unordered pair is visited
+// once: the home cell against itself (j after i) and against the 13 cells of
+// a half shell of its neighbours (offsets after (0,0,0) in z, y, x order);
+// the other 13 neighbours see this cell from their own half shells.  The 14
+// cells are staged in shared memory, warps take home particles, lanes take
+// the staged partners.
 // ---------------------------------------------------------------------------
 constexpr int kStage = 2048;  // staged partners per pass (32 KB)
 
@@ -196,15 +200,37 @@ __global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ c
                                                      double *__restrict__ partial)
 {
     __shared__ uint4 stage[kStage];
-    __shared__ Runs runs;
+    __shared__ int rs[14], re[14];  // start of each staged cell, inclusive end of its items
     __shared__ double red[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
-        int total = 0;
-        if (w == 0) total = warp_runs(cs, T, cx, cy, cz, runs);
+        if (w == 0) {
+            // lane 0: the home cell; lanes 1 .. 13: offsets 14 .. 26 of the
+            // 3 x 3 x 3 block in (z, y, x) order, i.e. those after (0, 0, 0)
+            int len = 0, st = 0;
+            if (lane < 14) {
+                const int k = lane == 0 ? 13 : 13 + lane;
+                const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+                int x = cx + dx, y = cy + dy, z = cz + dz;
+                x += (x < 0) ? T : 0;
+                x -= (x >= T) ? T : 0;
+                y += (y < 0) ? T : 0;
+                y -= (y >= T) ? T : 0;
+                z += (z < 0) ? T : 0;
+                z -= (z >= T) ? T : 0;
+                const int cell = (z * T + y) * T + x;
+                st = cs[cell];
+                len = cs[cell + 1] - st;
+            }
+            const int inc = warp_inclusive_scan(len);
+            if (lane < 14) {
+                rs[lane] = st;
+                re[lane] = inc;
+            }
+        }
         __syncthreads();
-        total = runs.end[17];
+        const int total = re[13];
         const int h0 = cs[c], h1 = cs[c + 1];
         Acc<F32> acc;
         for (int base = 0; base < total; base += kStage) {
@@ -212,24 +238,31 @@ __global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ c
             for (int f = threadIdx.x; f < nst; f += blockDim.x) {
                 const int g = base + f;
                 int r = 0;
-                while (g >= runs.end[r]) ++r;
-                stage[f] = cpos[runs.start[r] + g - (r ? runs.end[r - 1] : 0)];
+                while (g >= re[r]) ++r;
+                stage[f] = cpos[rs[r] + g - (r ? re[r - 1] : 0)];
             }
             __syncthreads();
             for (int i = h0 + w; i < h1; i += 8) {
                 const uint4 p = cpos[i];
                 const int t = (int)tag_species(p.w);
-                for (int f = lane; f < nst; f += 32) pair_acc<F32>(p, stage[f], p.w, R2, t, ff, fd, acc);
+                const int hi = i - h0;  // the home cell's items come first
+                for (int f = lane; f < nst; f += 32) {
+                    const int g = base + f;
+                    if (g <= hi) continue;  // within the home cell: partners after i only
+                    pair_acc<F32>(p, stage[f], 0xFFFFFFFFu, R2, t, ff, fd, acc);
+                }
             }
             __syncthreads();
         }
-        double e = warp_sum(acc.ev());
+        double e;
+        if constexpr (F32) e = (double)warp_sum(acc.e);
+        else e = warp_sum(acc.ev());
         if (lane == 0) red[w] = e;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int k = 0; k < 8; ++k) s += red[k];
-            partial[c] = s;
+            double sum = 0.0;
+            for (int k = 0; k < 8; ++k) sum += red[k];
+            partial[c] = sum;
         }
         __syncthreads();
     }
@@ -262,9 +295,11 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int64_t n, in
 //   dE/deps_ab (half of each ordered pair) += 2 (s^12 - s^6),
 //   dE/dsigma_ab (same) += (12 rep - 6 att) / (2 sigma_ab).
 // One warp per home particle; the per-cell scalars go to `partial` rows of
-// width 2 + 2 S^2: [E, virial, deps..., dsigma...].
+// width 2 + 2 S^2: [E, virial, deps..., dsigma...].  NS: partner species
+// kept in registers (the species count when it is 1 or 2, else kMaxSpecies).
+// FP32 mode sums per lane and across the warp in FP32, per CTA in FP64.
 // ---------------------------------------------------------------------------
-template <bool F32>
+template <bool F32, int NS>
 __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpos, const int32_t *__restrict__ cs,
                                                    int T, int64_t ncell, uint64_t R2, int S, const FieldF ff,
                                                    const FieldD fd, double inv_h, const int64_t *__restrict__ d_n,
@@ -276,9 +311,9 @@ __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpo
     __shared__ double red[8][kW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int width = 2 + 2 * S * S;
-    int64_t base_s[kMaxSpecies];
-    {
-        int64_t b = 0;
+    __shared__ long long base_s[kMaxSpecies];  // first species-major row of each species
+    if (threadIdx.x == 0) {
+        long long b = 0;
         for (int s = 0; s < kMaxSpecies; ++s) {
             base_s[s] = b;
             b += (s < S) ? d_n[s] : 0;
@@ -296,8 +331,9 @@ __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpo
             const uint4 p = cpos[i];
             const int t = (int)tag_species(p.w);
             R fx = 0, fy = 0, fz = 0;
-            CSum sE, sW, sEps[kMaxSpecies], sSig[kMaxSpecies];
-            double dE = 0, dW = 0, dEps[kMaxSpecies] = {}, dSig[kMaxSpecies] = {};
+            R aE = 0, aW = 0, aEps[NS], aSig[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) aEps[q] = aSig[q] = 0;
             int r = 0;
             for (int g = lane; g < total; g += 32) {
                 while (g >= runs.end[r]) ++r;
@@ -323,16 +359,14 @@ __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpo
                 const R uw = (R)0.5 * rdu;
                 const R ge = (R)2 * (s6 * s6 - s6);
                 const R gs = (R)0.5 * ((R)12 * rep - (R)6 * att);
-                if constexpr (F32) {
-                    sE.add(ue);
-                    sW.add(uw);
-                    sEps[ts].add(ge);
-                    sSig[ts].add(gs);
-                } else {
-                    dE += ue;
-                    dW += uw;
-                    dEps[ts] += ge;
-                    dSig[ts] += gs;
+                aE += ue;
+                aW += uw;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    if (q == ts) {
+                        aEps[q] += ge;
+                        aSig[q] += gs;
+                    }
                 }
             }
             const double gx = warp_sum((double)fx), gy = warp_sum((double)fy), gz = warp_sum((double)fz);
@@ -342,19 +376,22 @@ __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpo
                 dpos[3 * row + 1] = (float)(gy * inv_h);
                 dpos[3 * row + 2] = (float)(gz * inv_h);
             }
-            const double vE = warp_sum(F32 ? sE.value() : dE);
-            const double vW = warp_sum(F32 ? sW.value() : dW);
-            double ve[kMaxSpecies], vs[kMaxSpecies];
-            for (int ts = 0; ts < S; ++ts) {
-                ve[ts] = warp_sum(F32 ? sEps[ts].value() : dEps[ts]);
-                vs[ts] = warp_sum(F32 ? sSig[ts].value() : dSig[ts]);
+            const R vE = warp_sum(aE), vW = warp_sum(aW);
+            R ve[NS], vs[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                ve[q] = warp_sum(aEps[q]);
+                vs[q] = warp_sum(aSig[q]);
             }
             if (lane == 0) {
-                red[w][0] += vE;
-                red[w][1] += vW;
-                for (int ts = 0; ts < S; ++ts) {
-                    red[w][2 + t * S + ts] += ve[ts];
-                    red[w][2 + S * S + t * S + ts] += vs[ts];
+                red[w][0] += (double)vE;
+                red[w][1] += (double)vW;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    if (q < S) {
+                        red[w][2 + t * S + q] += (double)ve[q];
+                        red[w][2 + S * S + t * S + q] += (double)vs[q];
+                    }
                 }
             }
         }
@@ -423,7 +460,6 @@ gcmc_status total_energy(gcmc_ctx *ctx, double *energy)
     GCMC_CUDA(ctx, cudaMemcpyAsync(&e, ctx->d_red + ctx->ncell, sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
     GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    e *= 0.5;
     ctx->energy = e;
     ctx->energy_valid = true;
     GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice,
@@ -445,12 +481,19 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
     const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
     double *part = ctx->d_red;
     double *res = ctx->d_red + (size_t)ctx->ncell * width;
-    if (ctx->precision == GCMC_FP32)
-        k_cell_grad<true><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S,
-                                                      ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part);
-    else
-        k_cell_grad<false><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S,
-                                                       ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part);
+#define GCMC_GRAD(F, NSP)                                                                                   \
+    k_cell_grad<F, NSP><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S, \
+                                                     ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part)
+    if (ctx->precision == GCMC_FP32) {
+        if (S == 1) GCMC_GRAD(true, 1);
+        else if (S == 2) GCMC_GRAD(true, 2);
+        else GCMC_GRAD(true, kMaxSpecies);
+    } else {
+        if (S == 1) GCMC_GRAD(false, 1);
+        else if (S == 2) GCMC_GRAD(false, 2);
+        else GCMC_GRAD(false, kMaxSpecies);
+    }
+#undef GCMC_GRAD
     k_sum_partials<<<1, 1024, 0, ctx->stream>>>(part, ctx->ncell, width, res);
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());

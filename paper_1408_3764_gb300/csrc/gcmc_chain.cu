@@ -483,13 +483,36 @@ struct Chain {
     // pair term is computed and then masked by the cutoff test.  The cutoff
     // is decided on the FP32 squared distance except inside a thin band
     // around rc^2, where the exact integer squared distance decides.
+    // Per-evaluation constants of the FP32 item: the pair table entry of a
+    // single-species chain and the band around rc^2 (registers, not shared
+    // memory, inside the item loop).
+    struct ItemK {
+        float c4e, sig2, r2lo, r2hi;
+        bool single;
+    };
+
+    __device__ __forceinline__ ItemK item_consts() const
+    {
+        ItemK K;
+        K.single = a.S == 1;
+        K.c4e = a.ff.c4e[0];
+        K.sig2 = a.ff.sig2[0];
+        K.r2lo = a.r2lo;
+        K.r2hi = a.r2hi;
+        return K;
+    }
+
     template <int SIDES>
     __device__ __forceinline__ void item32(const Trial &t, const uint4 &q, bool valid, uint32_t fl,
-                                           float &acc, float &mag) const
+                                           const ItemK &K, float &acc, float &mag) const
     {
         const bool use = valid && (q.w != t.Po.w);
-        const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
-        const float c4e = a.ff.c4e[kk], sig2 = a.ff.sig2[kk];
+        float c4e = K.c4e, sig2 = K.sig2;
+        if (!K.single) {
+            const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
+            c4e = a.ff.c4e[kk];
+            sig2 = a.ff.sig2[kk];
+        }
         // SIDES 1: the old position only (deletion); 2: the new only
         // (insertion); 3: both (displacement)
         const uint4 &P0 = (SIDES == 2) ? t.Pn : t.Po;
@@ -512,19 +535,24 @@ struct Chain {
             }
             const uint32_t need = (SIDES == 3) ? (side ? kNew : kOld) : (SIDES == 2 ? kNew : kOld);
             const float r2f = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            bool in = use && (fl & need) && (r2f < a.r2lo);
-            if (use && (fl & need) && r2f >= a.r2lo && r2f <= a.r2hi) {
-                const unsigned long long g = (unsigned long long)((long long)ex * ex) +
-                                             (unsigned long long)((long long)ey * ey) +
-                                             (unsigned long long)((long long)ez * ez);
-                in = g < a.R2;
+            const bool want = use && (fl & need);
+            bool in = want && (r2f < K.r2lo);
+            // inside the thin band around rc^2 the exact integer test decides
+            const bool band = want && r2f >= K.r2lo && r2f <= K.r2hi;
+            if (__any_sync(0xffffffffu, band)) {
+                if (band) {
+                    const unsigned long long g = (unsigned long long)((long long)ex * ex) +
+                                                 (unsigned long long)((long long)ey * ey) +
+                                                 (unsigned long long)((long long)ez * ez);
+                    in = g < a.R2;
+                }
             }
             const float r2 = in ? r2f : 1e30f;
             const float s2 = __fdividef(sig2, r2);
             const float s6 = s2 * s2 * s2;
             const float cs = c4e * s6;
             float u = cs * (s6 - 1.f), m = cs * (s6 + 1.f);
-            if (ex == 0 && ey == 0 && ez == 0) u = m = __int_as_float(0x7f800000);
+            if (r2f == 0.f) u = m = __int_as_float(0x7f800000);  // r = 0 (every separation exactly 0)
             const bool neg = (SIDES == 1) || (SIDES == 3 && side == 0);
             acc += in ? (neg ? -u : u) : 0.f;
             mag += in ? m : 0.f;
@@ -547,13 +575,13 @@ struct Chain {
     };
 
     template <bool P32>
-    __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, float &acc,
-                                         float &mag, double &de, double &da) const
+    __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, const ItemK &K,
+                                         float &acc, float &mag, double &de, double &da) const
     {
         if constexpr (P32) {
-            if (t.type == 0) item32<3>(t, q, valid, fl, acc, mag);
-            else if (t.type == 1) item32<2>(t, q, valid, fl, acc, mag);
-            else item32<1>(t, q, valid, fl, acc, mag);
+            if (t.type == 0) item32<3>(t, q, valid, fl, K, acc, mag);
+            else if (t.type == 1) item32<2>(t, q, valid, fl, K, acc, mag);
+            else item32<1>(t, q, valid, fl, K, acc, mag);
         } else if (valid && q.w != t.Po.w) {
             FF e0 = {0.f, 0.f};
             float u0 = 0.f;
@@ -596,6 +624,7 @@ struct Chain {
         const int ib = warp_inclusive_scan(nb) + __shfl_sync(0xffffffffu, ia, 31);
         const int P = __shfl_sync(0xffffffffu, ib, 31);
         const int lo = (P * j) / G, hi = (P * (j + 1)) / G;
+        const ItemK K = item_consts();
         for (int base = lo; base < hi; base += 32 * KU) {
             int cell[KU], slot[KU], ncl[KU];
             uint32_t flg[KU];
@@ -644,7 +673,7 @@ struct Chain {
                         o.last = q[u];
                     }
                 }
-                item<P32>(t, q[u], v, flg[u], acc, mag, de, da);
+                item<P32>(t, q[u], v, flg[u], K, acc, mag, de, da);
             }
         }
         if constexpr (P32) {

@@ -217,6 +217,16 @@ def _cpu_workers(a):
     return max(1, min(16, n))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of x over the ranks of the default process group (the
+    job's time is its slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -482,9 +492,7 @@ def main():
     clocks = clk.summary()
     total_ms = sum(times)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
     K = len(chains)
     value = ws * a.steps * K * M / (total_ms / 1e3)
     stats = last[0]

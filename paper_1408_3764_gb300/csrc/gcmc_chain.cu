@@ -881,8 +881,10 @@ __device__ __forceinline__ bool still_valid(const Chain<F32> &C, const Shared &s
         }
     }
     if (__any_sync(0xffffffffu, bad)) return false;
-    if (t.type != 1 && __any_sync(0xffffffffu, nchanged)) {
-        // N changed: the move stands only if the same particle is chosen
+    (void)nchanged;
+    if (t.type != 1) {
+        // the move stands only if the counts at its turn pick the same
+        // particle (the evaluation may have used predicted counts)
         const int *ns = sh.ns_ring[m % kRS];
         const WordRec &W = C.words(m);
         int s = 0, idx = -1, possible = 1;
@@ -1055,6 +1057,34 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 tc.m[p] = mm;
                 tc.c0[p] = c0;
                 __threadfence_block();
+            }
+            __syncwarp();
+            if (j == 0 && a.S == 1) {
+                // predicted N at the move's turn (one species): lane i looks
+                // at the pending move c0 + i; an insertion or deletion whose
+                // evaluation is in and that the FP32 test would accept
+                // counts +1 or -1.  The particle pick uses the prediction;
+                // the committer checks the pick against the actual N.
+                const int go = tc.go[p], mm = tc.m[p], c0 = tc.c0[p];
+                if (go == 1 && mm > c0) {
+                    const int k = c0 + lane;
+                    int d = 0;
+                    if (k < mm) {
+                        const WordRec &Wk = C.words(k);
+                        const uint32_t w0 = Wk.w[0];
+                        const int ty = (w0 < a.thr_disp) ? 0 : ((w0 < a.thr_ins) ? 1 : 2);
+                        const Slot &Sk = sh.slots[k % kRS];
+                        if (ty != 0 && vload(Sk.tag) == k + 1 && vload(Sk.arrive) == G && Sk.t.possible) {
+                            float dU = 0.f;
+                            for (int q = 0; q < G; ++q) dU += F32 ? Sk.ph[q] : (float)Sk.pd[q];
+                            const float lnK = (ty == 1) ? a.lnzv_f[0] - sh.ln_n1[0] : sh.ln_n[0] - a.lnzv_f[0];
+                            if (Wk.lnu < lnK - (float)a.beta * dU) d = (ty == 1) ? 1 : -1;
+                        }
+                    }
+                    const int dn = __popc(__ballot_sync(0xffffffffu, d > 0)) - __popc(__ballot_sync(0xffffffffu, d < 0));
+                    if (lane == 0) tc.ns[p][0] = max(0, tc.ns[p][0] + dn);
+                    __threadfence_block();
+                }
             }
             // the whole leader warp reaches the team barrier together: the
             // barrier counts warps, not lanes

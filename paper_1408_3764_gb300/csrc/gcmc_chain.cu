@@ -1059,30 +1059,35 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 __threadfence_block();
             }
             __syncwarp();
-            if (j == 0 && a.S == 1) {
-                // predicted N at the move's turn (one species): lane i looks
-                // at the pending move c0 + i; an insertion or deletion whose
-                // evaluation is in and that the FP32 test would accept
-                // counts +1 or -1.  The particle pick uses the prediction;
-                // the committer checks the pick against the actual N.
+            if (j == 0) {
+                // predicted counts at the move's turn: lane i looks at the
+                // pending move c0 + i; an insertion or deletion whose
+                // evaluation is in and that the FP32 test would accept counts
+                // +1 or -1 for its species.  The particle pick uses the
+                // prediction; the committer checks the pick against the
+                // actual counts.
                 const int go = tc.go[p], mm = tc.m[p], c0 = tc.c0[p];
                 if (go == 1 && mm > c0) {
                     const int k = c0 + lane;
-                    int d = 0;
+                    int d = 0, sk = 0;
                     if (k < mm) {
                         const WordRec &Wk = C.words(k);
                         const uint32_t w0 = Wk.w[0];
                         const int ty = (w0 < a.thr_disp) ? 0 : ((w0 < a.thr_ins) ? 1 : 2);
                         const Slot &Sk = sh.slots[k % kRS];
                         if (ty != 0 && vload(Sk.tag) == k + 1 && vload(Sk.arrive) == G && Sk.t.possible) {
+                            sk = Sk.t.s;
                             float dU = 0.f;
                             for (int q = 0; q < G; ++q) dU += F32 ? Sk.ph[q] : (float)Sk.pd[q];
-                            const float lnK = (ty == 1) ? a.lnzv_f[0] - sh.ln_n1[0] : sh.ln_n[0] - a.lnzv_f[0];
+                            const float lnK = (ty == 1) ? a.lnzv_f[sk] - sh.ln_n1[sk] : sh.ln_n[sk] - a.lnzv_f[sk];
                             if (Wk.lnu < lnK - (float)a.beta * dU) d = (ty == 1) ? 1 : -1;
                         }
                     }
-                    const int dn = __popc(__ballot_sync(0xffffffffu, d > 0)) - __popc(__ballot_sync(0xffffffffu, d < 0));
-                    if (lane == 0) tc.ns[p][0] = max(0, tc.ns[p][0] + dn);
+                    for (int q = 0; q < a.S; ++q) {
+                        const int dn = __popc(__ballot_sync(0xffffffffu, d > 0 && sk == q)) -
+                                       __popc(__ballot_sync(0xffffffffu, d < 0 && sk == q));
+                        if (lane == 0) tc.ns[p][q] = max(0, tc.ns[p][q] + dn);
+                    }
                     __threadfence_block();
                 }
             }

@@ -65,6 +65,9 @@ def lib():
         L.orc_set_energy.argtypes = [vp, d]
         L.orc_get_energy.argtypes = [vp]
         L.orc_get_energy.restype = d
+        L.orc_set_virial.argtypes = [vp, d]
+        L.orc_get_virial.argtypes = [vp]
+        L.orc_get_virial.restype = d
         L.orc_move_words.argtypes = [u64, u64, u32, vp]
         L.orc_run_moves.argtypes = [vp, u64, u32, u64, i64, vp, d, vp, vp]
         L.orc_run_moves.restype = C.c_int
@@ -97,7 +100,7 @@ class Stats(C.Structure):
     _fields_ = [("attempted", C.c_int64 * 3), ("accepted", C.c_int64 * 3),
                 ("flagged", C.c_int64), ("moves_done", C.c_int64), ("energy", C.c_double),
                 ("sum_energy", C.c_double), ("sum_n", C.c_double),
-                ("n", C.c_int64 * MAX_SPECIES)]
+                ("n", C.c_int64 * MAX_SPECIES), ("virial", C.c_double), ("sum_virial", C.c_double)]
 
 
 def philox4x32_10(counter, key) -> np.ndarray:
@@ -241,6 +244,13 @@ class System:
 
     def energy(self) -> float:
         return lib().orc_get_energy(self._h)
+
+    def set_virial(self, W: float):
+        """Running virial sum_{i<j} r U'(r); NaN lets run_moves compute it."""
+        lib().orc_set_virial(self._h, float(W))
+
+    def virial(self) -> float:
+        return lib().orc_get_virial(self._h)
 
     def run_moves(self, seed, first, n_moves, p_disp, p_ins, p_del, max_disp, beta, log_z,
                   tol=1e-12, chain=0, trace=True):

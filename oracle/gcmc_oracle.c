@@ -129,6 +129,7 @@ typedef struct {
     int64_t *cell_alloc;
     orc_ref **cell;
     double E;          /* running total energy */
+    double W;          /* running virial sum_{i<j} r U'(r) (NaN: not set) */
 } orc_sys;
 
 /* Cells per side, Sec. 3.2.2: the largest T with S = L/T >= rc, and T = 3
@@ -338,12 +339,14 @@ int orc_build(orc_sys *sys, const double *pos, const int32_t *type, int64_t n,
     free(cellid);
     free(ref);
     sys->E = NAN;
+    sys->W = NAN;
     return 0;
 }
 
-/* Energy of one pair with exact cutoff decision; adds |rep|+|att| to *uabs. */
-static double pair_energy(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3],
-                          int tb, double *uabs)
+/* Energy of one pair with exact cutoff decision; adds |rep|+|att| to *uabs
+ * and, when wsum is given, the pair's virial term r U'(r) to *wsum. */
+static double pair_energy_w(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3],
+                            int tb, double *uabs, double *wsum)
 {
     int64_t d[3];
     uint64_t g = 0;
@@ -358,7 +361,14 @@ static double pair_energy(const orc_sys *sys, const uint32_t A[3], int ta, const
     double rep, att;
     double u = orc_lj(r2, sys->eps[ta * sys->S + tb], sys->sigma[ta * sys->S + tb], &rep, &att);
     if (uabs) *uabs += rep + att;
+    if (wsum) *wsum += sqrt(r2) * orc_lj_dr(r2, sys->eps[ta * sys->S + tb], sys->sigma[ta * sys->S + tb]);
     return u;
+}
+
+static double pair_energy(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3],
+                          int tb, double *uabs)
+{
+    return pair_energy_w(sys, A, ta, B, tb, uabs, NULL);
 }
 
 /* Energy of a particle of species t at grid position P against every
@@ -381,11 +391,12 @@ double orc_energy_brute(const orc_sys *sys, const uint32_t P[3], int t, int excl
 /* The same energy restricted to the 27 cells around the cell of P
  * (Algorithms 6 and 7; Sec. 3.2: the home cell and its 26 neighbours).
  * T >= 3 makes the 27 cells distinct. */
-double orc_energy_cells(const orc_sys *sys, const uint32_t P[3], int t, int excl_s,
-                        int64_t excl_i, double *uabs)
+static double energy_cells_w(const orc_sys *sys, const uint32_t P[3], int t, int excl_s,
+                             int64_t excl_i, double *uabs, double *wsum)
 {
     double e = 0.0;
     if (uabs) *uabs = 0.0;
+    if (wsum) *wsum = 0.0;
     int T = sys->T;
     int cx = cell_coord(P[0], T), cy = cell_coord(P[1], T), cz = cell_coord(P[2], T);
     for (int oz = -1; oz <= 1; ++oz)
@@ -396,10 +407,16 @@ double orc_energy_cells(const orc_sys *sys, const uint32_t P[3], int t, int excl
                 for (int64_t k = 0; k < sys->cell_len[c]; ++k) {
                     orc_ref r = sys->cell[c][k];
                     if (r.s == excl_s && r.i == excl_i) continue;
-                    e += pair_energy(sys, P, t, &sys->pos[r.s][3 * r.i], r.s, uabs);
+                    e += pair_energy_w(sys, P, t, &sys->pos[r.s][3 * r.i], r.s, uabs, wsum);
                 }
             }
     return e;
+}
+
+double orc_energy_cells(const orc_sys *sys, const uint32_t P[3], int t, int excl_s,
+                        int64_t excl_i, double *uabs)
+{
+    return energy_cells_w(sys, P, t, excl_s, excl_i, uabs, NULL);
 }
 
 /* Trial energies for m real positions (quantised by the grid rule).
@@ -577,10 +594,14 @@ typedef struct {
     double sum_energy;
     double sum_n;
     int64_t n[ORC_MAX_S];
+    double virial;      /* running virial after the last move */
+    double sum_virial;  /* sum over the moves of the running virial */
 } orc_stats;
 
 void orc_set_energy(orc_sys *sys, double E) { sys->E = E; }
 double orc_get_energy(const orc_sys *sys) { return sys->E; }
+void orc_set_virial(orc_sys *sys, double W) { sys->W = W; }
+double orc_get_virial(const orc_sys *sys) { return sys->W; }
 
 /* The eight random words of move m of chain `chain`: two Philox blocks
  * with counter (m_lo, m_hi, chain, block) and key (seed_lo, seed_hi). */
@@ -608,12 +629,17 @@ void orc_move_words(uint64_t seed, uint64_t m, uint32_t chain, uint32_t w[8])
  * The cell list follows Sec. 3.2.5 (swap-with-last removal, append);
  * a deleted index is refilled by the last index of its species.
  * A trial is flagged when |ln u - ln A| <= beta * tol * uabs + 1e-12 * (1 + |ln A|).
+ * Alongside the energy the chain keeps the virial W = sum_{i<j} r U'(r) (the
+ * pair sum behind the virial pressure P = rho k T - W / (3V), Sec. 3.1.1):
+ * each trial's dW is the same 27-cell sum with r U'(r) in place of U.
  * Returns 0, or -1 when the energy is not set. */
 int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, int64_t n_moves,
                   const orc_mix *mix, double tol, orc_trace *trace, orc_stats *st)
 {
     memset(st, 0, sizeof(*st));
     if (!(sys->E == sys->E)) return -1;
+    /* the running virial starts from the full sum over the 27 cells */
+    if (!(sys->W == sys->W)) orc_energy_grad(sys, NULL, NULL, NULL, NULL, &sys->W, 0);
     int S = sys->S;
     uint64_t thr_disp = (uint64_t)(mix->p_disp * ORC_TWO32);
     uint64_t thr_ins = (uint64_t)((mix->p_disp + mix->p_ins) * ORC_TWO32);
@@ -634,7 +660,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
         memset(&tr, 0, sizeof(tr));
         tr.type = (uint8_t)type;
         tr.index = -1;
-        double dU = 0.0, lnA = -INFINITY, uabs = 0.0;
+        double dU = 0.0, lnA = -INFINITY, uabs = 0.0, dW = 0.0;
         int s = 0;
         int64_t i = -1;
         int possible = 1;
@@ -655,10 +681,11 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
                     int64_t step = (int64_t)(((uint64_t)w[2 + a] * span) >> 32) - D;
                     Pn[a] = (uint32_t)((int64_t)Po[a] + step);
                 }
-                double ua0 = 0.0, ua1 = 0.0;
-                double e_old = orc_energy_cells(sys, Po, s, s, i, &ua0);
-                double e_new = orc_energy_cells(sys, Pn, s, s, i, &ua1);
+                double ua0 = 0.0, ua1 = 0.0, w0 = 0.0, w1 = 0.0;
+                double e_old = energy_cells_w(sys, Po, s, s, i, &ua0, &w0);
+                double e_new = energy_cells_w(sys, Pn, s, s, i, &ua1, &w1);
                 dU = e_new - e_old;
+                dW = w1 - w0;
                 uabs = ua0 + ua1;
                 lnA = -mix->beta * dU;
             }
@@ -667,7 +694,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
             Pn[0] = w[2];
             Pn[1] = w[3];
             Pn[2] = w[4];
-            dU = orc_energy_cells(sys, Pn, s, -1, -1, &uabs);
+            dU = energy_cells_w(sys, Pn, s, -1, -1, &uabs, &dW);
             i = sys->n[s];
             lnA = mix->log_z[s] + lnV - log((double)(sys->n[s] + 1)) - mix->beta * dU;
         } else {
@@ -676,7 +703,9 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
                 possible = 0;
             } else {
                 i = (int64_t)(((uint64_t)w[1] * (uint64_t)sys->n[s]) >> 32);
-                dU = -orc_energy_cells(sys, &sys->pos[s][3 * i], s, s, i, &uabs);
+                double w0 = 0.0;
+                dU = -energy_cells_w(sys, &sys->pos[s][3 * i], s, s, i, &uabs, &w0);
+                dW = -w0;
                 lnA = log((double)sys->n[s]) - mix->log_z[s] - lnV - mix->beta * dU;
             }
         }
@@ -718,6 +747,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
                 sys->n[s]--;
             }
             sys->E += dU;
+            sys->W += dW;
         }
         if (trace) {
             tr.dU = dU;
@@ -732,10 +762,12 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
         int64_t Nn = 0;
         for (int q = 0; q < S; ++q) Nn += sys->n[q];
         st->sum_energy += sys->E;
+        st->sum_virial += sys->W;
         st->sum_n += (double)Nn;
         st->moves_done++;
     }
     st->energy = sys->E;
+    st->virial = sys->W;
     for (int q = 0; q < S; ++q) st->n[q] = sys->n[q];
     return 0;
 }

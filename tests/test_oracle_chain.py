@@ -192,3 +192,75 @@ def test_chain_is_counter_based_resumable():
     sa, sb = a.state(), b.state()
     for x, y in zip(sa, sb):
         assert np.array_equal(x, y)
+
+
+def test_running_virial_equals_the_recomputed_virial():
+    """The chain's running virial W = sum_{i<j} r U'(r), kept by adding each
+    accepted trial's dW, equals W recomputed from the final configuration
+    (all pairs, analytic derivative) up to the rounding of the increments;
+    its per-move sum is the running value summed over the moves."""
+    L, rc = 11.0, 2.5
+    pos = _relaxed(500, L, 5)
+    types = (np.arange(500) % 3 == 0).astype(np.int32)
+    eps, sigma = W.lorentz_berthelot([1.0, 0.8], [1.0, 1.1])
+    s = O.System(L, rc, eps, sigma)
+    s.build(pos, types)
+    s.set_energy(s.total_energy())
+    W0 = s.energy_grad(brute=True)["virial"]
+    _, st1 = s.run_moves(13, 0, 20_000, 0.5, 0.25, 0.25, 0.3, 1 / 1.3, [-2.0, -2.5], trace=False)
+    Wf = s.energy_grad(brute=True)["virial"]
+    assert st1.virial == pytest.approx(Wf, rel=1e-9, abs=1e-9 * abs(W0))
+    assert st1.accepted[1] > 0 and st1.accepted[2] > 0
+    assert s.virial() == st1.virial
+    # one more move: the sum over the moves grows by the running value
+    _, st2 = s.run_moves(13, 20_000, 1, 0.5, 0.25, 0.25, 0.3, 1 / 1.3, [-2.0, -2.5], trace=False)
+    assert st2.sum_virial == pytest.approx(st2.virial, rel=1e-15)
+
+
+def test_ideal_gas_virial_is_zero():
+    L = 8.0
+    s = O.System(L, 2.5, [[0.0]], [[1.0]])
+    s.build(W.uniform_positions(50, L, 6), np.zeros(50, np.int32))
+    s.set_energy(0.0)
+    _, st = s.run_moves(3, 0, 5_000, 0.4, 0.3, 0.3, 0.5, 1.0, [math.log(0.1)], trace=False)
+    assert st.virial == 0.0 and st.sum_virial == 0.0
+
+
+def test_low_density_virial_matches_the_pair_integral():
+    """Low-density interacting gas: the pair correlation is exp(-beta U(r)), so
+    <W> = <N (N-1)> / (2V) * 4 pi int_0^rc r^3 U'(r) exp(-beta U(r)) dr up to
+    O(rho) corrections (a few per cent here) -- the virial route of the
+    pressure P = rho k T - <W> / (3V) for the truncated potential."""
+    from scipy.integrate import quad
+
+    beta, rc = 1.0 / 1.2, 2.5
+
+    def du(r):
+        return 4 * (-12 * r ** -13 + 6 * r ** -7)
+
+    I = 4 * math.pi * quad(lambda r: r ** 3 * du(r) * math.exp(-beta * 4 * (r ** -12 - r ** -6)),
+                           0.5, rc, points=[1.0, 1.12], limit=400)[0]
+    z = 0.02
+    L = (8000.0) ** (1 / 3)
+    V = L ** 3
+    s = O.System(L, rc, [[1.0]], [[1.0]])
+    n0 = 170
+    s.build(W.uniform_positions(n0, L, 8), np.zeros(n0, np.int32))
+    s.set_energy(s.total_energy())
+    s.run_moves(9, 0, 100_000, 0.2, 0.4, 0.4, 1.0, beta, [math.log(z)], trace=False)  # settle
+    means, want = [], []
+    n = None
+    for k in range(16):
+        tr, st = s.run_moves(9, 100_000 + k * 100_000, 100_000, 0.2, 0.4, 0.4, 1.0, beta, [math.log(z)])
+        if n is None:
+            n0k = int(st.n[0]) - int((tr["accepted"] & (tr["type"] == 1)).sum()) + \
+                int((tr["accepted"] & (tr["type"] == 2)).sum())
+        else:
+            n0k = int(n[-1])
+        n = _n_trajectory(tr, n0k).astype(float)
+        means.append(st.sum_virial / st.moves_done)
+        want.append((n * (n - 1)).mean() / (2 * V) * I)
+    means, want = np.array(means), np.array(want)
+    err = means.std(ddof=1) / math.sqrt(len(means))
+    assert I > 0  # attraction (U' > 0 beyond the minimum) dominates at T* = 1.2: the pressure drops
+    assert abs(means.mean() - want.mean()) < max(5 * err, 0.06 * abs(want.mean())), (means.mean(), want.mean(), err)

@@ -270,7 +270,7 @@ def run_reference(a):
 class Runner:
     """The chains of one workload on the GPU, and one step of the hot path."""
 
-    def __init__(self, chains, precision, dev, rank, host_inputs=False):
+    def __init__(self, chains, precision, dev, rank, host_inputs=False, virial=False):
         import torch
         from paper_1408_3764_gb300.gcmc import Batch, Box, Mix
         self.torch = torch
@@ -278,7 +278,7 @@ class Runner:
         self.dev = dev
         self.stream = torch.cuda.current_stream(dev)
         self.boxes = [Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev) for w in chains]
-        self.mixes = [Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z) for w in chains]
+        self.mixes = [Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z, virial=virial) for w in chains]
         self.seeds = [w.seed + 7919 * rank for w in chains]  # replicas: independent chains per rank
         self.batch = Batch(self.boxes) if len(chains) > 1 else None
         self.pos_h = [torch.from_numpy(w.positions()).pin_memory() for w in chains]
@@ -555,6 +555,13 @@ def main():
             r2.close()
             compare["isotherm_batched_" + other] = {"moves_per_s": K * M / (c2[0] / 1e3),
                                                      "step_moves_per_s": K * M / (t2[0] / 1e3)}
+            # the same isotherm keeping the running virial (virial pressure)
+            r3 = Runner(chains, a.precision, dev, 0, virial=True)
+            r3.step(0, M)
+            t3, c3, _ = _time_steps(r3, 1, 1, M, flush)
+            r3.close()
+            compare["isotherm_batched_%s_virial" % a.precision] = {
+                "moves_per_s": K * M / (c3[0] / 1e3), "step_moves_per_s": K * M / (t3[0] / 1e3)}
         base = compare.get("plain_fp64_single_chain_2048")
         if base:
             compare["value_over_plain_fp64_single_chain"] = value / base["step_moves_per_s"]

@@ -79,7 +79,20 @@ typedef struct {
     double max_disp;                   /* displacement half-width delta, 0 <= delta < L/2 */
     double beta;                       /* 1 / kT */
     double log_z[GCMC_MAX_SPECIES];    /* ln z_s = beta mu_s - 3 ln Lambda_s */
+    int32_t flags;                     /* GCMC_MIX_* bits; 0: energy only */
+    int32_t reserved;                  /* must be 0 */
 } gcmc_move_mix;
+
+/* Also keep the running virial W = sum_{i<j} r U'(r) over the pairs within
+ * rc (the pair sum of the virial pressure P = rho k T - W / (3V), updated
+ * on each accepted move, Sec. 3.1.2, and averaged on the GPU, Sec. 3.3.4):
+ * each accepted trial adds its dW, the same 27-cell sum with
+ * r U'(r) in place of U.  Reported in gcmc_move_stats.virial/sum_virial.
+ * The first run with the flag after a build, a restore or a run without it
+ * starts from the full 27-cell sum (the running energy is left as it is);
+ * later runs with it continue the running value.  The flag changes no
+ * decision and no energy: the moves and dU are those of a run without it. */
+#define GCMC_MIX_VIRIAL 1
 
 /* Counters of one gcmc_run_moves call (averages over the moves of the call). */
 typedef struct {
@@ -91,6 +104,8 @@ typedef struct {
     double sum_energy;     /* sum over the moves of the running energy after the move */
     double sum_n;          /* sum over the moves of N after the move */
     int64_t n[GCMC_MAX_SPECIES]; /* particles per species after the last move */
+    double virial;         /* running virial after the last move (GCMC_MIX_VIRIAL; else NaN) */
+    double sum_virial;     /* sum over the moves of the running virial after the move */
 } gcmc_move_stats;
 
 /* One record per move of gcmc_run_moves (32 bytes). */

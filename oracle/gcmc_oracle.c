@@ -630,7 +630,7 @@ void orc_move_words(uint64_t seed, uint64_t m, uint32_t chain, uint32_t w[8])
  * a deleted index is refilled by the last index of its species.
  * A trial is flagged when |ln u - ln A| <= beta * tol * uabs + 1e-12 * (1 + |ln A|).
  * Alongside the energy the chain keeps the virial W = sum_{i<j} r U'(r) (the
- * pair sum behind the virial pressure P = rho k T - W / (3V), Sec. 3.1.1):
+ * pair sum behind the virial pressure P = rho k T - W / (3V), Sec. 3.1.2):
  * each trial's dW is the same 27-cell sum with r U'(r) in place of U.
  * Returns 0, or -1 when the energy is not set. */
 int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, int64_t n_moves,

@@ -27,16 +27,20 @@ class Params(C.Structure):
                 ("cell_capacity", C.c_int32), ("reserved", C.c_int32)]
 
 
+MIX_VIRIAL = 1
+
+
 class MoveMix(C.Structure):
     _fields_ = [("p_disp", C.c_double), ("p_ins", C.c_double), ("p_del", C.c_double),
                 ("max_disp", C.c_double), ("beta", C.c_double),
-                ("log_z", C.c_double * MAX_SPECIES)]
+                ("log_z", C.c_double * MAX_SPECIES), ("flags", C.c_int32), ("reserved", C.c_int32)]
 
 
 class MoveStats(C.Structure):
     _fields_ = [("attempted", C.c_int64 * 3), ("accepted", C.c_int64 * 3), ("flagged", C.c_int64),
                 ("moves_done", C.c_int64), ("energy", C.c_double), ("sum_energy", C.c_double),
-                ("sum_n", C.c_double), ("n", C.c_int64 * MAX_SPECIES)]
+                ("sum_n", C.c_double), ("n", C.c_int64 * MAX_SPECIES), ("virial", C.c_double),
+                ("sum_virial", C.c_double)]
 
 
 class Geometry(C.Structure):

@@ -57,6 +57,8 @@ struct ChainOut {
     int pad;                // which waits gave up (1 leader, 2 committer, 4 keeper)
     long long reevaluated;  // moves evaluated again by the committer
     long long refines;      // trials decided in FP64 after the FP32 band test
+    double virial;          // running virial after the last move (virial runs)
+    double sum_virial;      // sum over the moves of the running virial
 };
 
 struct ChainArgs {
@@ -78,6 +80,7 @@ struct ChainArgs {
     double beta, lnV;
     double logz[kMaxSpecies];
     double tol;  // relative tolerance that defines "near the threshold"
+    int virial;  // also keep the running virial sum_{i<j} r U'(r)
     float lnzv_f[kMaxSpecies];
     FieldF ff;
     FieldD fd;
@@ -227,6 +230,8 @@ struct Slot {  // evaluators -> committer, one per move in flight
     uint4 last_val;               // the old cell's last entry (by the lane that met it)
     float ph[kGMax], pu[kGMax];   // per-warp FP32 sums: dU, uabs
     double pd[kGMax], pa[kGMax];  // per-warp FP64 sums: dU, uabs
+    float pw[kGMax];              // per-warp FP32 virial change (virial runs)
+    double pwd[kGMax];            // per-warp FP64 virial change (virial runs)
     int self_slot;                // the trial particle's slot in its old cell, -1 none
     int has_last;
     int c0;                       // moves committed when the evaluation started
@@ -246,6 +251,7 @@ struct LogRec {  // committer -> evaluation validity
 
 struct BookRec {  // committer -> keeper
     double dU64, lnA;  // dU when decided in FP64 or evaluated in FP64 mode
+    double dW;         // virial change of the trial (virial runs)
     float hi, lo;      // dU = hi + lo otherwise
     float uab;
     int use64;
@@ -281,7 +287,7 @@ __device__ __forceinline__ void vstore(int &x, int v) { *(volatile int *)&x = v;
 
 template <bool F32>
 __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const ChainArgs &a, int k, float sign,
-                                           FF &e, float &ua, double &de, double &da)
+                                           FF &e, float &ua, double &de, double &da, double &dw)
 {
     const int dx = (int)(P.x - q.x), dy = (int)(P.y - q.y), dz = (int)(P.z - q.z);
     // per-axis pre-filter: |d| >= rcg implies d^2 >= R2 (rcg^2 >= R2)
@@ -303,6 +309,7 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
         lj_f64(s, a.fd.c4e[k], a.fd.sig2[k], u, m);
         de += (double)sign * u;
         da += m;
+        dw -= (double)sign * (3.0 * m + 9.0 * u);  // r U'(r) = -12 rep + 6 att
     }
 }
 
@@ -324,7 +331,8 @@ __device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, 
 }
 
 // ---------------------------------------------------------------- the chain
-template <bool F32>
+// VIR: the evaluations also sum the virial change dW of each trial.
+template <bool F32, bool VIR>
 struct Chain {
     const ChainArgs &a;
     Shared &sh;
@@ -488,7 +496,7 @@ struct Chain {
     // memory, inside the item loop).
     struct ItemK {
         float c4e, sig2, r2lo, r2hi;
-        bool single;
+        bool single, vir;
     };
 
     __device__ __forceinline__ ItemK item_consts() const
@@ -499,12 +507,13 @@ struct Chain {
         K.sig2 = a.ff.sig2[0];
         K.r2lo = a.r2lo;
         K.r2hi = a.r2hi;
+        K.vir = VIR;
         return K;
     }
 
     template <int SIDES>
     __device__ __forceinline__ void item32(const Trial &t, const uint4 &q, bool valid, uint32_t fl,
-                                           const ItemK &K, float &acc, float &mag) const
+                                           const ItemK &K, float &acc, float &mag, float &wac) const
     {
         const bool use = valid && (q.w != t.Po.w);
         float c4e = K.c4e, sig2 = K.sig2;
@@ -556,6 +565,10 @@ struct Chain {
             const bool neg = (SIDES == 1) || (SIDES == 3 && side == 0);
             acc += in ? (neg ? -u : u) : 0.f;
             mag += in ? m : 0.f;
+            if (K.vir) {
+                const float w = -fmaf(3.f, m, 9.f * u);  // r U'(r) = -12 rep + 6 att
+                wac += in ? (neg ? -w : w) : 0.f;
+            }
         }
     }
 
@@ -568,26 +581,27 @@ struct Chain {
     // them, the trial particle's slot in its old cell and that cell's last
     // entry.
     struct Part {
-        float e, ua;
-        double de, da;
+        float e, ua, w;
+        double de, da, dw;
         int self_slot, has_last;
         uint4 last;
     };
 
     template <bool P32>
     __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, const ItemK &K,
-                                         float &acc, float &mag, double &de, double &da) const
+                                         float &acc, float &mag, float &wac, double &de, double &da,
+                                         double &dw) const
     {
         if constexpr (P32) {
-            if (t.type == 0) item32<3>(t, q, valid, fl, K, acc, mag);
-            else if (t.type == 1) item32<2>(t, q, valid, fl, K, acc, mag);
-            else item32<1>(t, q, valid, fl, K, acc, mag);
+            if (t.type == 0) item32<3>(t, q, valid, fl, K, acc, mag, wac);
+            else if (t.type == 1) item32<2>(t, q, valid, fl, K, acc, mag, wac);
+            else item32<1>(t, q, valid, fl, K, acc, mag, wac);
         } else if (valid && q.w != t.Po.w) {
             FF e0 = {0.f, 0.f};
             float u0 = 0.f;
             const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
-            if (fl & kOld) pair_terms<false>(t.Po, q, a, kk, -1.f, e0, u0, de, da);
-            if (fl & kNew) pair_terms<false>(t.Pn, q, a, kk, 1.f, e0, u0, de, da);
+            if (fl & kOld) pair_terms<false>(t.Po, q, a, kk, -1.f, e0, u0, de, da, dw);
+            if (fl & kNew) pair_terms<false>(t.Pn, q, a, kk, 1.f, e0, u0, de, da, dw);
         }
     }
 
@@ -598,8 +612,8 @@ struct Chain {
         o.self_slot = -1;
         o.has_last = 0;
         o.last = make_uint4(0, 0, 0, 0);
-        float acc = 0.f, mag = 0.f;
-        double de = 0.0, da = 0.0;
+        float acc = 0.f, mag = 0.f, wac = 0.f;
+        double de = 0.0, da = 0.0, dw = 0.0;
         const int nw = nwork(t);
         AxisList X, Y, Z;
         X.n = Y.n = Z.n = 3;
@@ -673,17 +687,21 @@ struct Chain {
                         o.last = q[u];
                     }
                 }
-                item<P32>(t, q[u], v, flg[u], K, acc, mag, de, da);
+                item<P32>(t, q[u], v, flg[u], K, acc, mag, wac, de, da, dw);
             }
         }
+        o.w = 0.f;
+        o.dw = 0.0;
         if constexpr (P32) {
             o.e = warp_sum(acc);
             o.ua = warp_sum(mag);
+            if (K.vir) o.w = warp_sum(wac);
             o.de = o.da = 0.0;
         } else {
             o.e = o.ua = 0.f;
             o.de = warp_sum(de);
             o.da = warp_sum(da);
+            if (K.vir) o.dw = warp_sum(dw);
         }
         return o;
     }
@@ -846,8 +864,8 @@ __device__ __forceinline__ bool box_within(const uint4 &X0, const uint4 &X1, con
 // committed move in [c0, m) touched its cells or wrote its particle's record,
 // and the current particle counts pick the same particle (or, for a move
 // that was impossible, still make it impossible).
-template <bool F32>
-__device__ __forceinline__ bool still_valid(const Chain<F32> &C, const Shared &sh, const Trial &t, int c0, int m,
+template <bool F32, bool VIR>
+__device__ __forceinline__ bool still_valid(const Chain<F32, VIR> &C, const Shared &sh, const Trial &t, int c0, int m,
                                             int T, int lane)
 {
     bool bad = false;
@@ -930,7 +948,7 @@ struct TeamCtl {
 // the committer; a move the committer finds invalid goes back to its team,
 // ahead of the team's new moves.  KU: slots per work cell a lane loads at
 // once.
-template <bool F32, int G, int NTEAM, int LOOK, int KU>
+template <bool F32, bool VIR, int G, int NTEAM, int LOOK, int KU>
 __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
     static_assert(G <= kGMax && LOOK < kRS && NTEAM <= 15, "team shape");
@@ -959,7 +977,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         }
         return;
     }
-    Chain<F32> C(a, sh, cnt);
+    Chain<F32, VIR> C(a, sh, cnt);
     const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
     const int n = a.n_moves;
     const int keeper_warp = EW + 1;
@@ -1099,7 +1117,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             const int m = tc.m[p];
             const Trial t = C.make_trial(m, tc.ns[p]);
             Slot &S = sh.slots[m % kRS];
-            const typename Chain<F32>::Part P = C.template eval_part<F32, KU>(t, j, G);
+            const typename Chain<F32, VIR>::Part P = C.template eval_part<F32, KU>(t, j, G);
             if (P.self_slot >= 0) S.self_slot = P.self_slot;
             if (P.has_last) {
                 S.last_val = P.last;
@@ -1110,9 +1128,11 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 if constexpr (F32) {
                     S.ph[j] = P.e;
                     S.pu[j] = P.ua;
+                    S.pw[j] = P.w;
                 } else {
                     S.pd[j] = P.de;
                     S.pa[j] = P.da;
+                    S.pwd[j] = P.dw;
                 }
             }
             __syncwarp();
@@ -1170,30 +1190,36 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             // the whole warp decides alike
             FF e = {0.f, 0.f};
             float uab = 0.f;
-            double de = 0.0, da = 0.0;
+            double de = 0.0, da = 0.0, dW = 0.0;
             if constexpr (F32) {
                 FF v = {lane < G ? S.ph[lane] : 0.f, 0.f};
                 float u = lane < G ? S.pu[lane] : 0.f;
+                float w = (VIR && lane < G) ? S.pw[lane] : 0.f;
 #pragma unroll
                 for (int o = kGMax / 2; o > 0; o >>= 1) {
-                    FF w;
-                    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-                    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-                    v = ff_add(v, w);
+                    FF x;
+                    x.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+                    x.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+                    v = ff_add(v, x);
                     u += __shfl_xor_sync(0xffffffffu, u, o);
+                    w += __shfl_xor_sync(0xffffffffu, w, o);
                 }
                 e.hi = __shfl_sync(0xffffffffu, v.hi, 0);
                 e.lo = __shfl_sync(0xffffffffu, v.lo, 0);
                 uab = __shfl_sync(0xffffffffu, u, 0);
+                dW = (double)__shfl_sync(0xffffffffu, w, 0);
             } else {
                 double v = lane < G ? S.pd[lane] : 0.0, u = lane < G ? S.pa[lane] : 0.0;
+                double w = (VIR && lane < G) ? S.pwd[lane] : 0.0;
 #pragma unroll
                 for (int o = kGMax / 2; o > 0; o >>= 1) {
                     v += __shfl_xor_sync(0xffffffffu, v, o);
                     u += __shfl_xor_sync(0xffffffffu, u, o);
+                    w += __shfl_xor_sync(0xffffffffu, w, o);
                 }
                 de = __shfl_sync(0xffffffffu, v, 0);
                 da = __shfl_sync(0xffffffffu, u, 0);
+                dW = __shfl_sync(0xffffffffu, w, 0);
                 e.hi = __double2float_rn(de);
                 uab = __double2float_rn(da);
             }
@@ -1208,9 +1234,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 // decide in FP64: in FP32 mode the whole trial is evaluated
                 // again in FP64 (pair terms and sums)
                 if constexpr (F32) {
-                    const typename Chain<F32>::Part Q = C.template eval_part<false, 4>(t, 0, 1);
+                    const typename Chain<F32, VIR>::Part Q = C.template eval_part<false, 4>(t, 0, 1);
                     de = Q.de;
                     da = Q.da;
+                    dW = Q.dw;
                 }
                 const WordRec &W = C.words(m);
                 const double lnu = log(uniform53(W.w[6], W.w[7]));
@@ -1245,6 +1272,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             if (lane == 0) {
                 BookRec &B = sh.book[m % kRS];
                 B.dU64 = de;
+                B.dW = dW;
                 B.hi = e.hi;
                 B.lo = e.lo;
                 B.use64 = use64;
@@ -1267,6 +1295,9 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
     } else if (warp == keeper_warp) {
         // ------------------------------------------------------------ keeper
         double E = *a.d_energy, sumE = 0.0;
+        // the running virial, for the chains of the launch that keep it
+        const bool vir = VIR && a.virial;
+        double Wv = vir ? a.d_energy[1] : 0.0, sumW = 0.0;
         long long sumN = 0, att0 = 0, att1 = 0, att2 = 0, acc0 = 0, acc1 = 0, acc2 = 0;
         long long flagged = 0, reeval = 0, refines = 0, Ncur = 0;
         for (int q = 0; q < kMaxSpecies; ++q) Ncur += sh.n[q];
@@ -1311,6 +1342,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                         acc1 += type == 1;
                         acc2 += type == 2;
                         E += B.use64 ? B.dU64 : (double)B.hi + (double)B.lo;
+                        Wv += B.dW;
                         Ncur += (type == 1) - (type == 2);
                     }
                     if (a.trace) {
@@ -1334,6 +1366,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                         a.trace[mb] = tr;
                     }
                     sumE += E;
+                    sumW += Wv;
                     sumN += Ncur;
                     vstore(sh.booked, mb + 1);
                 }
@@ -1376,7 +1409,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             o.sum_n = (double)sumN;
             o.reevaluated = reeval;
             o.refines = refines;
+            o.virial = vir ? Wv : NAN;
+            o.sum_virial = vir ? sumW : NAN;
             *a.d_energy = E;
+            if (vir) a.d_energy[1] = Wv;
         }
     }
     __syncthreads();
@@ -1400,14 +1436,14 @@ constexpr int kNumConfigs = 4;
 static const int kConfigG[kNumConfigs] = {7, 4, 3, 2};
 static const int kConfigT[kNumConfigs] = {2, 3, 4, 6};
 
-template <bool F32>
+template <bool F32, bool VIR>
 static void *chain_kernel(int config)
 {
     switch (config) {
-    case 1: return (void *)k_chain<F32, 4, 3, 6, 2>;
-    case 2: return (void *)k_chain<F32, 3, 4, 8, 2>;
-    case 3: return (void *)k_chain<F32, 2, 6, 12, 3>;
-    default: return (void *)k_chain<F32, 7, 2, 4, 2>;
+    case 1: return (void *)k_chain<F32, VIR, 4, 3, 6, 2>;
+    case 2: return (void *)k_chain<F32, VIR, 3, 4, 8, 2>;
+    case 3: return (void *)k_chain<F32, VIR, 2, 6, 12, 3>;
+    default: return (void *)k_chain<F32, VIR, 7, 2, 4, 2>;
     }
 }
 
@@ -1460,6 +1496,7 @@ static void fill_args(ChainArgs &a, const ChainJob &j, ChainOut *out)
     a.lnV = std::log(ctx->V);
     for (int s = 0; s < kMaxSpecies; ++s) a.logz[s] = s < ctx->S ? mix->log_z[s] : 0.0;
     a.tol = ctx->precision == GCMC_FP32 ? 1e-5 : 1e-12;
+    a.virial = (mix->flags & GCMC_MIX_VIRIAL) ? 1 : 0;
     for (int s = 0; s < kMaxSpecies; ++s) a.lnzv_f[s] = (float)(a.logz[s] + a.lnV);
     a.ff = ctx->ff;
     a.fd = ctx->fd;
@@ -1547,7 +1584,11 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
     }
     size_t smem = 16;
     for (auto &j : jobs) smem = std::max(smem, ((size_t)j.ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16);
-    void *kern = f32 ? chain_kernel<true>(config) : chain_kernel<false>(config);
+    // the virial sums are compiled in only when a chain of the launch keeps it
+    bool vir = false;
+    for (auto &j : jobs) vir |= (j.mix.flags & GCMC_MIX_VIRIAL) != 0;
+    void *kern = f32 ? (vir ? chain_kernel<true, true>(config) : chain_kernel<true, false>(config))
+                     : (vir ? chain_kernel<false, true>(config) : chain_kernel<false, false>(config));
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
@@ -1624,6 +1665,13 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
             j.agg.sum_energy += o.sum_energy;
             j.agg.sum_n += o.sum_n;
             j.agg.energy = o.energy;
+            if (j.mix.flags & GCMC_MIX_VIRIAL) {
+                j.agg.virial = o.virial;
+                j.agg.sum_virial += o.sum_virial;
+                ctx->virial = o.virial;
+            } else {
+                ctx->virial_valid = false;  // the moves did not keep it up to date
+            }
             for (int q = 0; q < kMaxSpecies; ++q) {
                 j.agg.n[q] = o.n[q];
                 ctx->n_host[q] = o.n[q];
@@ -1731,6 +1779,11 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
         st = total_energy(ctx, nullptr);
         if (st != GCMC_OK) return st;
     }
+    const bool vir = (mix->flags & GCMC_MIX_VIRIAL) != 0;
+    if (vir && !ctx->virial_valid) {
+        st = total_energy(ctx, nullptr, true);
+        if (st != GCMC_OK) return st;
+    }
     static thread_local LaunchBufs bufs;
     std::vector<ChainJob> jobs(1);
     ChainJob &j = jobs[0];
@@ -1743,6 +1796,8 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
     j.mix = *mix;
     j.trace = trace;
     j.result = GCMC_OK;
+    j.agg.virial = vir ? ctx->virial : NAN;
+    j.agg.sum_virial = vir ? 0.0 : NAN;
     ctx->last_refetch = 0;
     ctx->last_refines = 0;
     std::string err;
@@ -1781,6 +1836,13 @@ gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint6
                 return st;
             }
         }
+        if ((mixes[k].flags & GCMC_MIX_VIRIAL) && !ctxs[k]->virial_valid) {
+            st = total_energy(ctxs[k], nullptr, true);
+            if (st != GCMC_OK) {
+                if (err) *err = ctxs[k]->err;
+                return st;
+            }
+        }
     }
     static thread_local LaunchBufs bufs;
     std::vector<ChainJob> jobs(K);
@@ -1802,6 +1864,9 @@ gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint6
         j.n_moves = n_moves;
         j.mix = mixes[k];
         j.result = GCMC_OK;
+        const bool vir = (mixes[k].flags & GCMC_MIX_VIRIAL) != 0;
+        j.agg.virial = vir ? ctxs[k]->virial : NAN;
+        j.agg.sum_virial = vir ? 0.0 : NAN;
         ctxs[k]->last_refetch = 0;
         ctxs[k]->last_refines = 0;
     }

@@ -160,7 +160,7 @@ gcmc_status gcmc_create(const gcmc_params *p, void *stream, gcmc_ctx **out)
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     ctx->smem_optin = (size_t)optin;
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_energy, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_energy, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_n, sizeof(int64_t) * kMaxSpecies);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_n, 0, sizeof(int64_t) * kMaxSpecies);
@@ -230,7 +230,7 @@ gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, in
     const double ps = mix->p_disp + mix->p_ins + mix->p_del;
     if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
         !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L) || !(mix->beta >= 0.0) ||
-        !std::isfinite(mix->beta))
+        !std::isfinite(mix->beta) || (mix->flags & ~GCMC_MIX_VIRIAL) != 0 || mix->reserved != 0)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: bad move mix");
     for (int s = 0; s < ctx->S; ++s)
         if (!std::isfinite(mix->log_z[s]))
@@ -399,6 +399,7 @@ gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const ui
     ctx->n_build = N;
     ctx->energy = energy;
     ctx->energy_valid = !std::isnan(energy);
+    ctx->virial_valid = false;
     if (ctx->energy_valid)
         GCMC_CUDA(ctx, cudaMemcpy(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice));
     return GCMC_OK;
@@ -517,7 +518,8 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
         const gcmc_move_mix *mix = &mixes[k];
         const double ps = mix->p_disp + mix->p_ins + mix->p_del;
         if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
-            !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < b->ctxs[k]->L) || !(mix->beta >= 0.0)) {
+            !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < b->ctxs[k]->L) || !(mix->beta >= 0.0) ||
+            (mix->flags & ~GCMC_MIX_VIRIAL) != 0 || mix->reserved != 0) {
             b->err = "gcmc_batch_run_moves: bad move mix";
             return GCMC_ERR_INVALID_ARG;
         }

@@ -42,7 +42,7 @@ struct gcmc_ctx {
     uint4 *pos_by_id = nullptr;   // S * maxN
     int64_t *d_n = nullptr;       // S counts
     int32_t *d_status = nullptr;  // device status bits
-    double *d_energy = nullptr;   // running energy (1 double)
+    double *d_energy = nullptr;   // running energy and running virial (2 doubles)
     // compact layout (valid when compact_valid)
     bool compact_valid = false;
     int32_t *cell_start = nullptr;  // ncell + 1
@@ -60,6 +60,8 @@ struct gcmc_ctx {
 
     double energy = 0.0;
     bool energy_valid = false;
+    double virial = 0.0;      // running virial sum_{i<j} r U'(r)
+    bool virial_valid = false;
     int64_t launches = 0;  // kernels this context has launched
     int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
     int64_t last_refines = 0;
@@ -91,7 +93,10 @@ gcmc_status relayout(gcmc_ctx *ctx, int new_cap, int64_t new_maxN);
 // energy.cu
 gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,
                          const int64_t *exclude, int64_t m, double *out, double *out_abs);
-gcmc_status total_energy(gcmc_ctx *ctx, double *energy);
+// Full-system energy and virial (27-cell sums).  Both become the chain's
+// running values; with virial_only the running energy is left as it is and
+// only the virial is set.
+gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only = false);
 gcmc_status total_energy_noalloc(gcmc_ctx *ctx, double *energy_dev);
 gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
                         double *virial);

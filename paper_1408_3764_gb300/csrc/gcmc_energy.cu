@@ -22,22 +22,24 @@ template <bool F32>
 struct Acc;
 template <>
 struct Acc<true> {
-    float e = 0.f, a = 0.f;
+    float e = 0.f, a = 0.f, w = 0.f;  // energy, |terms|, virial r U'(r) = -(3 m + 9 u)
     __device__ __forceinline__ void add(float u, float m)
     {
         e += u;
         a += m;
+        w -= fmaf(3.f, m, 9.f * u);
     }
     __device__ __forceinline__ double ev() const { return (double)e; }
     __device__ __forceinline__ double av() const { return (double)a; }
 };
 template <>
 struct Acc<false> {
-    double e = 0.0, a = 0.0;
+    double e = 0.0, a = 0.0, w = 0.0;
     __device__ __forceinline__ void add(double u, double m)
     {
         e += u;
         a += m;
+        w -= 3.0 * m + 9.0 * u;
     }
     __device__ __forceinline__ double ev() const { return e; }
     __device__ __forceinline__ double av() const { return a; }
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ c
 {
     __shared__ uint4 stage[kStage];
     __shared__ int rs[14], re[14];  // start of each staged cell, inclusive end of its items
-    __shared__ double red[8];
+    __shared__ double red[8][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
@@ -254,15 +256,23 @@ __global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ c
             }
             __syncthreads();
         }
-        double e;
-        if constexpr (F32) e = (double)warp_sum(acc.e);
-        else e = warp_sum(acc.ev());
-        if (lane == 0) red[w] = e;
+        double e, vw;
+        if constexpr (F32) {
+            e = (double)warp_sum(acc.e);
+            vw = (double)warp_sum(acc.w);
+        } else {
+            e = warp_sum(acc.ev());
+            vw = warp_sum(acc.w);
+        }
+        if (lane == 0) {
+            red[w][0] = e;
+            red[w][1] = vw;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 2) {
             double sum = 0.0;
-            for (int k = 0; k < 8; ++k) sum += red[k];
-            partial[c] = sum;
+            for (int k = 0; k < 8; ++k) sum += red[k][threadIdx.x];
+            partial[2 * c + threadIdx.x] = sum;  // energy, virial
         }
         __syncthreads();
     }
@@ -440,11 +450,11 @@ gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *specie
     return GCMC_OK;
 }
 
-gcmc_status total_energy(gcmc_ctx *ctx, double *energy)
+gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
 {
     gcmc_status st = make_compact(ctx);
     if (st != GCMC_OK) return st;
-    st = ensure_red(ctx, (size_t)ctx->ncell + 8);
+    st = ensure_red(ctx, 2 * (size_t)ctx->ncell + 8);
     if (st != GCMC_OK) return st;
     const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
     if (ctx->precision == GCMC_FP32)
@@ -453,17 +463,24 @@ gcmc_status total_energy(gcmc_ctx *ctx, double *energy)
     else
         k_cell_energy<false><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2,
                                                          ctx->ff, ctx->fd, ctx->d_red);
-    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 1, ctx->d_red + ctx->ncell);
+    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 2, ctx->d_red + 2 * ctx->ncell);
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());
-    double e = 0.0;
-    GCMC_CUDA(ctx, cudaMemcpyAsync(&e, ctx->d_red + ctx->ncell, sizeof(double), cudaMemcpyDeviceToHost,
+    double ew[2] = {0.0, 0.0};
+    GCMC_CUDA(ctx, cudaMemcpyAsync(ew, ctx->d_red + 2 * ctx->ncell, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
     GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->energy = e;
-    ctx->energy_valid = true;
-    GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice,
-                                   ctx->stream));
+    const double e = ew[0];
+    ctx->virial = ew[1];
+    ctx->virial_valid = true;
+    if (virial_only) {
+        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy + 1, &ctx->virial, sizeof(double), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+    } else {
+        ctx->energy = e;
+        ctx->energy_valid = true;
+        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, ew, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
     GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (energy) *energy = e;
     return GCMC_OK;

@@ -39,6 +39,7 @@ class Mix:
     max_disp: float
     beta: float
     log_z: Sequence[float]
+    virial: bool = False  # also keep the running virial (stats virial, sum_virial)
 
     def to_c(self) -> MoveMix:
         m = MoveMix()
@@ -47,6 +48,8 @@ class Mix:
         lz = list(self.log_z)
         for s in range(MAX_SPECIES):
             m.log_z[s] = float(lz[s]) if s < len(lz) else 0.0
+        m.flags = _lib.MIX_VIRIAL if self.virial else 0
+        m.reserved = 0
         return m
 
 
@@ -54,7 +57,8 @@ def stats_dict(st: MoveStats, n_species: int) -> dict:
     return dict(attempted=list(st.attempted), accepted=list(st.accepted), flagged=int(st.flagged),
                 moves_done=int(st.moves_done), energy=float(st.energy),
                 sum_energy=float(st.sum_energy), sum_n=float(st.sum_n),
-                n=[int(st.n[s]) for s in range(n_species)])
+                n=[int(st.n[s]) for s in range(n_species)], virial=float(st.virial),
+                sum_virial=float(st.sum_virial))
 
 
 class Box:

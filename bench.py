@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the cutoff sweep figures")
+    ap.add_argument("--sweep-moves", type=int, default=100_000, help="moves per cutoff and precision")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the throughput kernels (trial energies, total energy, gradient, cell build)")
     ap.add_argument("--cpu-moves", type=int, default=0, help="oracle moves per chain in the CPU sample")
@@ -371,6 +373,28 @@ def _fp32_vs_fp64_agreement(w, M, dev):
             "flagged_and_refined": int((a["flagged"] & 1).sum())}
 
 
+def _cutoff_sweep(dev, flush, M):
+    """One chain of 87,296 particles in 131,072 sigma^3 at each cutoff of the
+    sweep, FP32 and FP64: chain moves/s (device time of the chain launch), the
+    27-cell candidates and the within-cutoff partners of a trial point."""
+    from paper_1408_3764_gb300 import workloads as W
+    out = {}
+    for rc in W.SWEEP_RC:
+        w = W.cutoff_sweep(rc)
+        T = max(3, int(w.L // rc))
+        row = {"T": T, "candidates_per_point": 27.0 * w.n / T ** 3,
+               "pairs_in_rc_per_point": 4.0 / 3.0 * math.pi * rc ** 3 * w.rho}
+        for prec in ("fp32", "fp64"):
+            r = _single_chain_rate(w, prec, M, dev, flush)
+            row[prec + "_moves_per_s"] = r["moves_per_s"]
+        out["%.2f" % rc] = row
+    base = out["%.2f" % W.SWEEP_RC[0]]
+    for row in out.values():
+        row["fp32_rate_vs_rc2.5"] = row["fp32_moves_per_s"] / base["fp32_moves_per_s"]
+    return {"workload": "lj-87296-V131072 (rho 0.666), T* 1.5, one chain, %d moves per point" % M,
+            "rc": out}
+
+
 def _kernel_figures(dev, flush, sm_mhz):
     """Throughput kernels on the million-particle mixture and the gradient
     workload: trial energies, full-system energy, gradient, cell build."""
@@ -568,6 +592,9 @@ def main():
         agreement = _fp32_vs_fp64_agreement(chains[-1], 20_000, dev)
     if rank == 0 and not a.no_kernels:
         kernels = _kernel_figures(dev, flush, clocks.get("sm_mhz"))
+    sweep = None
+    if rank == 0 and not a.no_sweep:
+        sweep = _cutoff_sweep(dev, flush, a.sweep_moves)
 
     cpu = None
     if pool is not None:
@@ -588,10 +615,12 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64",
                 "data": "synthetic (seeded uniform random positions)", "config": cfg,
                 "chain_moves_per_s": achieved, "team_shape": tuned[0],
+                "tuner_probe_ms": [float(x) for x in tuned[1]] if tuned[1] is not None else None,
                 "acceptance": acc, "final_n_total": int(sum(sum(s["n"]) for s in stats)),
                 "flagged": int(sum(s["flagged"] for s in stats)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "compare": compare, "fp32_vs_fp64": agreement, "kernels": kernels}
+                "clocks": clocks, "compare": compare, "fp32_vs_fp64": agreement, "kernels": kernels,
+                "cutoff_sweep": sweep}
         print(json.dumps(line))
     run.close()
     if ws > 1:

@@ -261,8 +261,9 @@ gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out);
 gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined);
 
 /* Team shape of the chain kernel (how its warps split the evaluation of
- * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape on
- * the first moves of the next gcmc_run_moves and keep the fastest.  Every
+ * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape
+ * during the next gcmc_run_moves (after a first quarter of its moves under
+ * shape 0) and keep the fastest.  Every
  * shape takes the same moves and decisions and reaches the same
  * configuration; in FP32 mode the pair terms are summed in a shape-dependent
  * order, so dU (and the running energy) may differ in the last bits.
@@ -290,14 +291,16 @@ gcmc_status gcmc_batch_destroy(gcmc_batch *batch);
 /* Moves first_move .. first_move + n_moves - 1 of every chain, as
  * gcmc_run_moves would run them one context at a time.  seeds, mixes:
  * host, n_chains each; stats: host, n_chains, or NULL.  On the first call
- * with the automatic team shape, the first moves are timed under every
- * shape and the fastest is kept.  Errors: as gcmc_run_moves, the first
+ * with the automatic team shape, the first quarter of the moves runs under
+ * shape 0, then every shape is timed on two short chunks (in ascending, then
+ * descending shape order) and the shape with the smallest total is kept.  Errors: as gcmc_run_moves, the first
  * failing chain's status (its context has the message); INVALID_ARG. */
 gcmc_status gcmc_batch_run_moves(gcmc_batch *batch, const uint64_t *seeds, uint64_t first_move, int64_t n_moves,
                                  const gcmc_move_mix *mixes, gcmc_move_stats *stats);
 
 /* Sets the team shape (-1 automatic, -2 leave unchanged) and reports the
- * current one and the per-shape probe times in ms of the last tuning (host,
+ * current one and the per-shape probe times in ms of the last tuning (the
+ * sum of the shape's two chunks; host,
  * GCMC_CHAIN_CONFIGS doubles, or NULL).  Errors: INVALID_ARG. */
 gcmc_status gcmc_batch_config(gcmc_batch *batch, int32_t set_config, int32_t *config_out, double *probe_ms);
 

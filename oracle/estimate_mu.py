@@ -37,7 +37,19 @@ def estimate(rho, T, rc, eps, sigma, fractions, n=1000, sweeps=150, widom=200_00
     return out
 
 
+def sweep():
+    """ln z along the cutoff sweep (87,296 particles in 131,072 sigma^3, T* 1.5)."""
+    e1, s1 = np.array([[1.0]]), np.array([[1.0]])
+    rho = W.SWEEP_N / W.SWEEP_V
+    vals = [estimate(rho, W.SWEEP_T, rc, e1, s1, [1.0], n=2000, sweeps=100, widom=100_000)[0]
+            for rc in W.SWEEP_RC]
+    print("SWEEP_LOGZ", [round(v, 4) for v in vals])
+    sys.stdout.flush()
+
+
 def main():
+    if sys.argv[1:] == ["sweep"]:
+        return sweep()
     e1, s1 = np.array([[1.0]]), np.array([[1.0]])
     em, sm = W.lorentz_berthelot([1.0, 0.8], [1.0, 1.2])
     print("C1", estimate(0.5, 1.2, 2.5, e1, s1, [1.0]))

@@ -1714,10 +1714,13 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
     return GCMC_OK;
 }
 
-// Runs the jobs with the given team shape, or -- config < 0 -- first times
-// a short chunk of moves under every shape and runs the rest with the
-// fastest (config returns the choice).  Every shape takes exactly the same
-// moves, so tuning never changes the chain.
+// Runs the jobs with the given team shape, or -- config < 0 -- picks one:
+// the first quarter of the moves runs under shape 0 (a fresh configuration
+// relaxes there, and its rates do not predict the rest), then every shape is
+// timed on short chunks, twice, in the orders 0 .. K-1 and K-1 .. 0 (the sum
+// cancels a steady drift of the chains), and the rest runs under the shape
+// with the smallest total (config returns the choice).  Every shape takes
+// exactly the same moves, so tuning never changes the chain.
 static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, bool f32, int &config,
                                   LaunchBufs &B, int64_t *launches, std::string *err, bool use_graph,
                                   double *probe_ms, double *dev_ms = nullptr)
@@ -1725,18 +1728,17 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
     if (config >= 0) return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);
     int64_t remaining = INT64_MAX;
     for (auto &j : jobs) remaining = std::min<int64_t>(remaining, j.n_moves - j.done);
-    const int64_t chunk = std::min<int64_t>(std::max<int64_t>(remaining / (4 * kNumConfigs), 256), 4096);
-    if (remaining < 2 * chunk * kNumConfigs) {
+    const int64_t chunk = std::min<int64_t>(std::max<int64_t>(remaining / (8 * kNumConfigs), 256), 2048);
+    if (remaining < 4 * chunk * kNumConfigs) {
         config = 0;
         return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);
     }
-    double best = 1e300;
-    int bc = 0;
-    for (int c = 0; c < kNumConfigs; ++c) {
+    // runs the next `count` moves of every job under shape c; returns its time
+    auto run_limited = [&](int c, int64_t count, float *ms_out) -> gcmc_status {
         std::vector<int64_t> saved(jobs.size());
         for (size_t k = 0; k < jobs.size(); ++k) {
             saved[k] = jobs[k].n_moves;
-            jobs[k].n_moves = std::min<int64_t>(jobs[k].n_moves, jobs[k].done + chunk);
+            jobs[k].n_moves = std::min<int64_t>(jobs[k].n_moves, jobs[k].done + count);
         }
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -1750,12 +1752,26 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (size_t k = 0; k < jobs.size(); ++k) jobs[k].n_moves = saved[k];
-        if (r != GCMC_OK) return r;
-        if (probe_ms) probe_ms[c] = ms;
-        if (ms < best) {
-            best = ms;
-            bc = c;
+        if (ms_out) *ms_out = ms;
+        return r;
+    };
+    const int64_t burn = std::min<int64_t>(remaining / 4, remaining - 3 * chunk * kNumConfigs);
+    gcmc_status r = run_limited(0, burn, nullptr);
+    if (r != GCMC_OK) return r;
+    double total[kNumConfigs] = {};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < kNumConfigs; ++i) {
+            const int c = pass == 0 ? i : kNumConfigs - 1 - i;
+            float ms = 0.f;
+            r = run_limited(c, chunk, &ms);
+            if (r != GCMC_OK) return r;
+            total[c] += ms;
         }
+    }
+    int bc = 0;
+    for (int c = 0; c < kNumConfigs; ++c) {
+        if (probe_ms) probe_ms[c] = total[c];
+        if (total[c] < total[bc]) bc = c;
     }
     config = bc;
     return run_jobs(jobs, st, f32, config, B, launches, err, use_graph, dev_ms);

@@ -13,6 +13,7 @@ the batched isotherm and the gradient workload of the hot-path scope.
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 from typing import List, Optional
 
@@ -28,6 +29,52 @@ def uniform_positions(n: int, L: float, seed: int) -> np.ndarray:
     """n positions uniform in [0, L)^3 (float64, shape (n, 3))."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.random((n, 3)) * L
+
+
+def separated_positions(n: int, L: float, dmin: float, seed: int) -> np.ndarray:
+    """n positions in the periodic box [0, L)^3 with no two closer than dmin
+    (minimum image): random sequential addition -- uniform candidates, each
+    kept if it keeps dmin from every position kept before.  The candidates
+    come from one PCG64 stream, so the result depends only on the arguments."""
+    return _separated(int(n), float(L), float(dmin), int(seed)).copy()
+
+
+@functools.lru_cache(maxsize=4)
+def _separated(n: int, L: float, dmin: float, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = max(1, int(L // dmin))  # hash cells of edge >= dmin: partners lie in the 27 around
+    h, half, d2 = L / g, 0.5 * L, dmin * dmin
+    cells = {}
+    out = []
+    while len(out) < n:
+        for px, py, pz in (rng.random((4096, 3)) * L).tolist():
+            cx, cy, cz = int(px / h) % g, int(py / h) % g, int(pz / h) % g
+            ok = True
+            for ix in ((cx - 1) % g, cx, (cx + 1) % g):
+                for iy in ((cy - 1) % g, cy, (cy + 1) % g):
+                    for iz in ((cz - 1) % g, cz, (cz + 1) % g):
+                        for qx, qy, qz in cells.get((ix, iy, iz), ()):
+                            dx, dy, dz = px - qx, py - qy, pz - qz
+                            dx = dx - L if dx > half else (dx + L if dx < -half else dx)
+                            dy = dy - L if dy > half else (dy + L if dy < -half else dy)
+                            dz = dz - L if dz > half else (dz + L if dz < -half else dz)
+                            if dx * dx + dy * dy + dz * dz < d2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                cells.setdefault((cx, cy, cz), []).append((px, py, pz))
+                out.append((px, py, pz))
+                if len(out) == n:
+                    break
+    arr = np.array(out, dtype=np.float64)
+    arr.setflags(write=False)
+    return arr
 
 
 def species_labels(n: int, fractions, seed: int) -> np.ndarray:
@@ -63,6 +110,7 @@ class Workload:
     moves: int = 10_000
     seed: int = 1
     L: float = field(default=0.0)
+    dmin: float = 0.0  # > 0: initial positions at least dmin apart (random sequential addition)
 
     def __post_init__(self):
         if self.L == 0.0:
@@ -73,6 +121,8 @@ class Workload:
         return 1.0 / self.temperature
 
     def positions(self) -> np.ndarray:
+        if self.dmin > 0.0:
+            return separated_positions(self.n, self.L, self.dmin, self.seed)
         return uniform_positions(self.n, self.L, self.seed)
 
     def types(self) -> np.ndarray:
@@ -98,6 +148,17 @@ LOGZ_C5 = (-1.193, -1.086)
 ISO_RHO = (0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7)
 ISO_LOGZ = (-2.9274, -2.7906, -2.7883, -2.7456, -2.7257, -2.7801, -2.7521, -2.7273, -2.7114,
             -2.729, -2.3514, -2.2062, -1.9642)
+
+
+# The cutoff sweep (Sec. 4, "Performance impact of different cutoffs"): a fixed
+# initial configuration of 87,296 particles in 131,072 sigma^3 (rho ~ 0.666)
+# with rc from 2.5 to 4.25 sigma.  The temperature is not printed; T* 1.5 keeps
+# the fluid supercritical at every cutoff.
+SWEEP_N = 87296
+SWEEP_V = 131072.0
+SWEEP_T = 1.5
+SWEEP_RC = (2.5, 2.75, 3.0, 3.25, 3.5, 3.75, 4.0, 4.25)
+SWEEP_LOGZ = (-0.6439, -0.7842, -0.8303, -0.9137, -0.8561, -0.9926, -1.1244, -1.0134)
 
 
 def c1_plain_fp64() -> Workload:
@@ -127,6 +188,16 @@ def c5_gradient() -> Workload:
     e, s = lorentz_berthelot([1.0, 0.8], [1.0, 1.2])
     return Workload("ljmix-262144-rho0.65-rc3.0", 1 << 18, 0.65, 3.0, 1.3, e, s, [0.8, 0.2],
                     list(LOGZ_C5), moves=0, seed=5)
+
+
+def cutoff_sweep(rc: float, moves: int = 1_000_000) -> Workload:
+    """87,296 particles, V = 131,072 (L = 50.80), T* 1.5, cutoff rc (one of
+    SWEEP_RC); one fixed initial configuration for every cutoff: random
+    sequential addition with pairs at least 0.9 sigma apart (seed 6)."""
+    k = SWEEP_RC.index(rc)
+    e, s = _single()
+    return Workload("lj-87296-V131072-rc%.2f" % rc, SWEEP_N, SWEEP_N / SWEEP_V, rc, SWEEP_T, e, s, [1.0],
+                    [SWEEP_LOGZ[k]], moves=moves, seed=6, L=SWEEP_V ** (1.0 / 3.0), dmin=0.9)
 
 
 def isotherm_chains(n_chains: int = 64, seed: int = 4, n_min: int = 500, n_max: int = 20000,

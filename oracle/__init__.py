@@ -76,6 +76,12 @@ def lib():
         L.orc_get_state.argtypes = [vp, vp, vp, vp]
         L.orc_widom.argtypes = [vp, C.c_int, d, u64, i64]
         L.orc_widom.restype = d
+        L.orc_micro_build.argtypes = [vp, d]
+        L.orc_micro_build.restype = C.c_int
+        L.orc_micro_state.argtypes = [vp, vp, vp]
+        L.orc_micro_state.restype = i64
+        L.orc_micro_per_side.argtypes = [vp]
+        L.orc_micro_per_side.restype = C.c_int
         _lib = L
     return _lib
 
@@ -280,6 +286,24 @@ class System:
 
     def widom(self, species, beta, seed, n) -> float:
         return lib().orc_widom(self._h, species, beta, seed, n)
+
+    def micro_build(self, edge: float = 1.0) -> int:
+        """Builds the microcells (Sec. 3.3) of the current particles; later
+        accepted moves keep them up to date.  Returns M (cells per side)."""
+        M = lib().orc_micro_build(self._h, float(edge))
+        if M < 0:
+            raise ValueError("bad microcell edge")
+        return M
+
+    def micro_state(self):
+        """(M, per-microcell counts, concatenated per-cell lists of (i << 8) | s,
+        largest count)."""
+        M = lib().orc_micro_per_side(self._h)
+        cnt = np.zeros(max(M ** 3, 1), np.int64)
+        n = int(self.counts().sum())
+        refs = np.zeros(max(n, 1), np.uint32)
+        mx = lib().orc_micro_state(self._h, _p(cnt), _p(refs))
+        return M, cnt[: M ** 3], refs[:n], int(mx)
 
 
 def lib_path() -> str:

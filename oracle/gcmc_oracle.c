@@ -130,6 +130,13 @@ typedef struct {
     orc_ref **cell;
     double E;          /* running total energy */
     double W;          /* running virial sum_{i<j} r U'(r) (NaN: not set) */
+    /* microcells (Sec. 3.3): M per side, an ordered reference list per
+     * microcell; mc_M = 0 while none are built */
+    int mc_M;
+    int64_t mc_ncell;
+    int64_t *mc_len;
+    int64_t *mc_alloc;
+    orc_ref **mc;
 } orc_sys;
 
 /* Cells per side, Sec. 3.2.2: the largest T with S = L/T >= rc, and T = 3
@@ -223,9 +230,22 @@ orc_sys *orc_create(double L, double rc, int S, const double *eps, const double 
     return sys;
 }
 
+static void micro_free(orc_sys *sys)
+{
+    for (int64_t c = 0; c < sys->mc_ncell; ++c) free(sys->mc[c]);
+    free(sys->mc);
+    free(sys->mc_len);
+    free(sys->mc_alloc);
+    sys->mc = NULL;
+    sys->mc_len = sys->mc_alloc = NULL;
+    sys->mc_M = 0;
+    sys->mc_ncell = 0;
+}
+
 void orc_destroy(orc_sys *sys)
 {
     if (!sys) return;
+    micro_free(sys);
     for (int s = 0; s < sys->S; ++s) free(sys->pos[s]);
     for (int64_t c = 0; c < sys->ncell; ++c) free(sys->cell[c]);
     free(sys->cell);
@@ -278,6 +298,86 @@ static void ensure_index(orc_sys *sys, int s, int64_t i)
     sys->cap[s] = nc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Microcells, Sec. 3.3: the box cut into M^3 cells of edge about one   */
+/* sigma, each holding an ordered list of its particles.  Reading: M =  */
+/* ceil(L / edge) cells per side of equal edge L / M (<= edge); the     */
+/* paper's unit cells with a thinner last cell give the same counts of  */
+/* cells per side.  The microcell of a grid coordinate X is             */
+/* floor(X * M / 2^32), as for the ordinary cells.                      */
+/* ------------------------------------------------------------------ */
+static int64_t micro_of(const orc_sys *sys, const uint32_t P[3])
+{
+    int M = sys->mc_M;
+    return ((int64_t)cell_coord(P[2], M) * M + cell_coord(P[1], M)) * M + cell_coord(P[0], M);
+}
+
+static void micro_append(orc_sys *sys, int64_t c, orc_ref r)
+{
+    if (sys->mc_len[c] == sys->mc_alloc[c]) {
+        int64_t na = sys->mc_alloc[c] ? 2 * sys->mc_alloc[c] : 4;
+        sys->mc[c] = (orc_ref *)realloc(sys->mc[c], (size_t)na * sizeof(orc_ref));
+        sys->mc_alloc[c] = na;
+    }
+    sys->mc[c][sys->mc_len[c]++] = r;
+}
+
+/* Deleting an ID from a microcell, Sec. 3.3.3: scan the cell's list for it,
+ * the last ID of the list takes its place, the counter drops by one. */
+static int micro_remove(orc_sys *sys, int64_t c, orc_ref r)
+{
+    int64_t n = sys->mc_len[c];
+    for (int64_t k = 0; k < n; ++k) {
+        if (sys->mc[c][k].s == r.s && sys->mc[c][k].i == r.i) {
+            sys->mc[c][k] = sys->mc[c][n - 1];
+            sys->mc_len[c] = n - 1;
+            return 0;
+        }
+    }
+    return -1;
+}
+
+/* Builds the microcells of the current particles (Sec. 3.3.1): every
+ * particle is added to the list of its microcell, species by species and
+ * index by index.  Returns M, or -1 for a bad edge.  Later accepted moves
+ * keep the lists up to date (orc_run_moves). */
+int orc_micro_build(orc_sys *sys, double edge)
+{
+    if (!(edge > 0.0)) return -1;
+    micro_free(sys);
+    double m = ceil(sys->L / edge);
+    if (m < 1.0) m = 1.0;
+    if (m > 1024.0) return -1;
+    sys->mc_M = (int)m;
+    sys->mc_ncell = (int64_t)sys->mc_M * sys->mc_M * sys->mc_M;
+    sys->mc_len = (int64_t *)calloc((size_t)sys->mc_ncell, sizeof(int64_t));
+    sys->mc_alloc = (int64_t *)calloc((size_t)sys->mc_ncell, sizeof(int64_t));
+    sys->mc = (orc_ref **)calloc((size_t)sys->mc_ncell, sizeof(orc_ref *));
+    for (int s = 0; s < sys->S; ++s)
+        for (int64_t i = 0; i < sys->n[s]; ++i) {
+            orc_ref r = {s, (int32_t)i};
+            micro_append(sys, micro_of(sys, &sys->pos[s][3 * i]), r);
+        }
+    return sys->mc_M;
+}
+
+/* Microcell state: per-cell counts and the concatenated per-cell lists
+ * encoded as (i << 8) | s (either may be NULL); returns the largest count. */
+int64_t orc_micro_state(const orc_sys *sys, int64_t *counts, uint32_t *refs)
+{
+    int64_t k = 0, mx = 0;
+    for (int64_t c = 0; c < sys->mc_ncell; ++c) {
+        if (counts) counts[c] = sys->mc_len[c];
+        if (sys->mc_len[c] > mx) mx = sys->mc_len[c];
+        if (refs)
+            for (int64_t j = 0; j < sys->mc_len[c]; ++j)
+                refs[k++] = ((uint32_t)sys->mc[c][j].i << 8) | (uint32_t)sys->mc[c][j].s;
+    }
+    return mx;
+}
+
+int orc_micro_per_side(const orc_sys *sys) { return sys->mc_M; }
+
 /* Binning, Sec. 3.2.1.  Particles keep the order in which they are given:
  * the index of a particle within its species is its rank among the input
  * particles of that species, and every cell lists its particles in input
@@ -289,6 +389,7 @@ int orc_build(orc_sys *sys, const double *pos, const int32_t *type, int64_t n,
 {
     for (int s = 0; s < sys->S; ++s) sys->n[s] = 0;
     for (int64_t c = 0; c < sys->ncell; ++c) sys->cell_len[c] = 0;
+    micro_free(sys);
     int64_t *cellid = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
     orc_ref *ref = (orc_ref *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_ref));
     for (int64_t p = 0; p < n; ++p) {
@@ -727,21 +828,35 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
                     cell_remove(sys, c0, r);
                     cell_append(sys, c1, r);
                 }
+                if (sys->mc_M) {
+                    int64_t m0 = micro_of(sys, Po), m1 = micro_of(sys, Pn);
+                    if (m0 != m1) {
+                        micro_remove(sys, m0, r);
+                        micro_append(sys, m1, r);
+                    }
+                }
                 for (int a = 0; a < 3; ++a) Po[a] = Pn[a];
             } else if (type == 1) {
                 ensure_index(sys, s, i);
                 for (int a = 0; a < 3; ++a) sys->pos[s][3 * i + a] = Pn[a];
                 sys->n[s]++;
                 cell_append(sys, cell_of(sys, Pn), r);
+                if (sys->mc_M) micro_append(sys, micro_of(sys, Pn), r);
             } else {
                 uint32_t *Pd = &sys->pos[s][3 * i];
                 cell_remove(sys, cell_of(sys, Pd), r);
+                if (sys->mc_M) micro_remove(sys, micro_of(sys, Pd), r);
                 int64_t last = sys->n[s] - 1;
                 if (i != last) {
                     uint32_t *Pl = &sys->pos[s][3 * last];
                     int64_t cl = cell_of(sys, Pl);
                     for (int64_t k = 0; k < sys->cell_len[cl]; ++k)
                         if (sys->cell[cl][k].s == s && sys->cell[cl][k].i == last) sys->cell[cl][k].i = (int32_t)i;
+                    if (sys->mc_M) {
+                        int64_t ml = micro_of(sys, Pl);
+                        for (int64_t k = 0; k < sys->mc_len[ml]; ++k)
+                            if (sys->mc[ml][k].s == s && sys->mc[ml][k].i == last) sys->mc[ml][k].i = (int32_t)i;
+                    }
                     for (int a = 0; a < 3; ++a) Pd[a] = Pl[a];
                 }
                 sys->n[s]--;

@@ -351,6 +351,34 @@ def _single_chain_rate(w, precision, M, dev, flush):
             "precision": precision, "n": w.n}
 
 
+def _micro_chain_rate(w, precision, M, dev, flush):
+    """Moves/s of one chain evaluated over the microcell list (Sec. 3.3; device
+    time of the chain launch) after a warm-up run of 20,000 moves."""
+    import torch
+    from paper_1408_3764_gb300.gcmc import Box, Mix
+    b = Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev)
+    mix = Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z)
+    pos = torch.from_numpy(w.positions()).to(dev)
+    typ = torch.from_numpy(w.types()).to(dev)
+    b.build_cells(pos, typ)
+    b.build_microcells(1.0)
+    b.run_moves_micro(w.seed, 0, min(M, 20_000), mix)
+    b.build_cells(pos, typ)
+    b.total_energy()
+    b.build_microcells(1.0)
+    flush.fill_(3)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run_moves_micro(w.seed + 1, 0, M, mix)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"moves_per_s": M / (ms / 1e3), "moves": M, "precision": precision, "n": w.n,
+            "microcells_per_side": b.microcells()[0]}
+
+
 def _fp32_vs_fp64_agreement(w, M, dev):
     """The same chain in FP32 and FP64 mode on the GPU: identical decisions,
     dU difference relative to uabs (the scale of the pair terms)."""
@@ -387,6 +415,8 @@ def _cutoff_sweep(dev, flush, M):
         for prec in ("fp32", "fp64"):
             r = _single_chain_rate(w, prec, M, dev, flush)
             row[prec + "_moves_per_s"] = r["moves_per_s"]
+        # the paper's microcell list: cube of (2D+1)^3 microcells of edge ~sigma
+        row["micro_fp32_moves_per_s"] = _micro_chain_rate(w, "fp32", M, dev, flush)["moves_per_s"]
         out["%.2f" % rc] = row
     base = out["%.2f" % W.SWEEP_RC[0]]
     for row in out.values():
@@ -571,6 +601,11 @@ def main():
             for prec in ("fp32", "fp64"):
                 compare["single_chain_131072_" + prec] = _single_chain_rate(W.c2_fp32_vs_fp64(), prec, 200_000,
                                                                             dev, flush)
+        # the same single chains evaluated over the microcell list (Sec. 3.3)
+        compare["micro_single_chain_2048_fp64"] = _micro_chain_rate(W.c1_plain_fp64(), "fp64", 10_000, dev, flush)
+        for prec in ("fp32", "fp64"):
+            compare["micro_single_chain_131072_" + prec] = _micro_chain_rate(W.c2_fp32_vs_fp64(), prec, 200_000,
+                                                                             dev, flush)
         if a.workload == "isotherm":
             other = "fp64" if a.precision == "fp32" else "fp32"
             r2 = Runner(chains, other, dev, 0)

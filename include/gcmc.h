@@ -186,6 +186,44 @@ gcmc_status gcmc_trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *s
 gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
                            const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
 
+/* Microcell list (Sec. 3.3): the box cut into M^3 microcells of edge about
+ * one sigma, each holding at most `capacity` particles in a slot array
+ * stored slot-major (slot k of every cell contiguous, Sec. 3.3.1).
+ * M = ceil(L / edge) cells per side of equal edge L / M (the paper's unit
+ * cells with a thinner last one have the same count); the microcell of grid
+ * coordinate X is floor(X * M / 2^32).  Builds the microcells of the
+ * current particles, listed species by species, index by index.
+ * capacity: 1 .. 15, or 0 = automatic (5, raised to the fullest cell's
+ * count and grown by gcmc_run_moves_micro when a move needs a fuller cell).
+ * Valid until a build, a restore or a gcmc_run_moves / batch run (which
+ * keep only the 27-cell lists); gcmc_run_moves_micro rebuilds them then.
+ * Errors: STATE (no cells), INVALID_ARG (edge, capacity, too many
+ * microcells for the chain's on-chip counters), CELL_OVERFLOW (a cell holds
+ * more than capacity, or more than 15), CUDA. */
+gcmc_status gcmc_build_microcells(gcmc_ctx *ctx, double edge, int32_t capacity);
+
+/* The microcells: per_side = M, capacity = slots per cell (host, or NULL);
+ * counts: host, M^3 bytes, or NULL; slots: host, capacity * M^3 records of
+ * four uint32 (X, Y, Z, tag), slot-major, or NULL (slots at or past a cell's
+ * count hold stale data).  Errors: STATE (none up to date), CUDA. */
+gcmc_status gcmc_microcells(gcmc_ctx *ctx, int64_t *per_side, int32_t *capacity, uint8_t *counts,
+                            uint32_t *slots);
+
+/* The chain of gcmc_run_moves evaluated over the microcell list (Sec. 3.3.3
+ * and 3.3.4): one CTA runs the moves one after another; each trial's energy
+ * is the sum over the (2D+1)^3 microcells around the old and the new
+ * position, D = 1 + floor((rcg - 1) M / 2^32) with rcg the smallest integer
+ * with rcg^2 >= the grid cutoff (every cell at most D cells away along each
+ * axis; all M when 2D+1 > M).  Same moves, decisions, trace and statistics
+ * as gcmc_run_moves (the flag GCMC_MIX_VIRIAL is not accepted); accepted
+ * moves update the microcells (append; removal by swap-with-last) and the
+ * 27-cell lists exactly as gcmc_run_moves does, so every other call stays
+ * valid.  Rebuilds stale microcells first with the last edge and capacity.
+ * Errors: as gcmc_run_moves; STATE when gcmc_build_microcells was never
+ * called; CELL_OVERFLOW when a microcell of fixed capacity is full. */
+gcmc_status gcmc_run_moves_micro(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
+                                 const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+
 /* Full-system cell-list energy E = 1/2 sum_i sum_{j != i in the 27 cells}
  * U(r_ij), r < rc (Sec. 3.1.1 computes the same sum over all pairs).
  * Also resets the running energy of the chain to this value.

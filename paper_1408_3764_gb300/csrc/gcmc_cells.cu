@@ -336,6 +336,7 @@ gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species
     ctx->order_valid = false;
     ctx->energy_valid = false;
     ctx->virial_valid = false;
+    ctx->mc_valid = false;
     if (hstatus & kStatusBadInput)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_build_cells: species out of range or coordinate not finite");
     const int maxc = (int)(hsmall[8] & 0xffffffff);

@@ -68,6 +68,7 @@ gcmc_status read_status(gcmc_ctx *ctx, int *bits)
 
 static void free_device(gcmc_ctx *ctx)
 {
+    micro_free(ctx);
     void *ptrs[] = {ctx->cell_pos, ctx->cell_count, ctx->pos_by_id, ctx->d_n, ctx->d_status,
                     ctx->d_energy, ctx->cell_start, ctx->cpos, ctx->order, ctx->scratch, ctx->d_red};
     for (void *p : ptrs)
@@ -235,7 +236,60 @@ gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, in
     for (int s = 0; s < ctx->S; ++s)
         if (!std::isfinite(mix->log_z[s]))
             return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: log_z not finite");
+    ctx->mc_valid = false;  // the chain below keeps the 27-cell lists only
     return run_moves(ctx, seed, first_move, n_moves, mix, stats, trace);
+}
+
+static gcmc_status check_mix(gcmc_ctx *ctx, const gcmc_move_mix *mix, int64_t n_moves, const char *who)
+{
+    if (!mix || n_moves < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad args");
+    const double ps = mix->p_disp + mix->p_ins + mix->p_del;
+    if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
+        !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L) || !(mix->beta >= 0.0) ||
+        !std::isfinite(mix->beta) || mix->flags != 0 || mix->reserved != 0)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad move mix");
+    for (int s = 0; s < ctx->S; ++s)
+        if (!std::isfinite(mix->log_z[s]))
+            return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": log_z not finite");
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_build_microcells(gcmc_ctx *ctx, double edge, int32_t capacity)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_build_microcells: cells not built");
+    if (!(edge > 0.0) || !std::isfinite(edge) || capacity < 0 || capacity > 15)
+        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_build_microcells: bad edge or capacity");
+    return micro_build(ctx, edge, capacity);
+}
+
+gcmc_status gcmc_microcells(gcmc_ctx *ctx, int64_t *per_side, int32_t *capacity, uint8_t *counts,
+                            uint32_t *slots)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->mc_valid) return fail(ctx, GCMC_ERR_STATE, "gcmc_microcells: no up-to-date microcells");
+    if (per_side) *per_side = ctx->mc_M;
+    if (capacity) *capacity = ctx->mc_cap;
+    if (counts)
+        GCMC_CUDA(ctx, cudaMemcpyAsync(counts, ctx->mc_count, (size_t)ctx->mc_ncell, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+    if (slots)
+        GCMC_CUDA(ctx, cudaMemcpyAsync(slots, ctx->mc_pos, (size_t)ctx->mc_cap * ctx->mc_ncell * sizeof(uint4),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_run_moves_micro(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
+                                 const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves_micro: cells not built");
+    if (!(ctx->mc_edge > 0.0))
+        return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves_micro: gcmc_build_microcells was never called");
+    gcmc_status st = check_mix(ctx, mix, n_moves, "gcmc_run_moves_micro");
+    if (st != GCMC_OK) return st;
+    return run_moves_micro(ctx, seed, first_move, n_moves, mix, stats, trace);
 }
 
 gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy)
@@ -400,6 +454,7 @@ gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const ui
     ctx->energy = energy;
     ctx->energy_valid = !std::isnan(energy);
     ctx->virial_valid = false;
+    ctx->mc_valid = false;
     if (ctx->energy_valid)
         GCMC_CUDA(ctx, cudaMemcpy(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice));
     return GCMC_OK;
@@ -525,6 +580,7 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
         }
     }
     if (n_moves == 0) return GCMC_OK;
+    for (gcmc_ctx *c : b->ctxs) c->mc_valid = false;  // the batched chain keeps the 27-cell lists only
     std::string err;
     gcmc_status st = run_batch(b->ctxs.data(), (int)b->ctxs.size(), seeds, first_move, n_moves, mixes, stats,
                                b->config, &b->launches, &err, b->stream, true, b->probe_ms, &b->last_ms);

@@ -65,7 +65,18 @@ struct gcmc_ctx {
     int64_t launches = 0;  // kernels this context has launched
     int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
     int64_t last_refines = 0;
-    int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)  // chain trials decided in FP64 after the FP32 band test (last run)
+    int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)
+
+    // ---- microcells (Sec. 3.3), valid while mc_valid
+    bool mc_valid = false;
+    double mc_edge = 0.0;     // requested edge (0: never built)
+    int mc_cap_req = 0;       // 0 = automatic
+    int mc_M = 0;             // microcells per side
+    int64_t mc_ncell = 0;     // mc_M^3
+    int mc_cap = 0;           // slots per microcell, as allocated (<= 15)
+    int mc_D = 0;             // half-width of the cube of microcells around a point
+    uint8_t *mc_count = nullptr;  // mc_ncell
+    uint4 *mc_pos = nullptr;      // mc_cap * mc_ncell, slot-major: slot k of cell c at k * mc_ncell + c
 
     std::string err;
 };
@@ -104,6 +115,11 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
 // chain.cu
 gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+// micro.cu
+gcmc_status micro_build(gcmc_ctx *ctx, double edge, int cap_req);
+gcmc_status run_moves_micro(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves,
+                            const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
+void micro_free(gcmc_ctx *ctx);
 gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
                       std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms,

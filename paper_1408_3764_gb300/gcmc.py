@@ -214,6 +214,41 @@ class Box:
             return stats, arr
         return stats
 
+    def build_microcells(self, edge: float = 1.0, capacity: int = 0) -> None:
+        """Microcell list of the current particles (Sec. 3.3)."""
+        check(self._lib.gcmc_build_microcells(self._h, float(edge), int(capacity)), self._h,
+              "gcmc_build_microcells")
+
+    def microcells(self):
+        """(M, capacity, counts [M^3] uint8, slots [capacity, M^3, 4] uint32 (X, Y, Z, tag))."""
+        M = C.c_int64()
+        cap = C.c_int32()
+        check(self._lib.gcmc_microcells(self._h, C.byref(M), C.byref(cap), None, None), self._h, "gcmc_microcells")
+        n3 = M.value ** 3
+        counts = np.zeros(n3, np.uint8)
+        slots = np.zeros((cap.value, n3, 4), np.uint32)
+        check(self._lib.gcmc_microcells(self._h, None, None, counts.ctypes.data_as(C.c_void_p),
+                                        slots.ctypes.data_as(C.c_void_p)), self._h, "gcmc_microcells")
+        return M.value, cap.value, counts, slots
+
+    def run_moves_micro(self, seed: int, first_move: int, n_moves: int, mix: Mix, trace: bool = False,
+                        check_status: bool = True):
+        """The chain of run_moves evaluated over the microcell list."""
+        cm = mix.to_c()
+        st = MoveStats()
+        tb = None
+        if trace:
+            tb = torch.empty((max(n_moves, 1), _lib.TRACE_BYTES), dtype=torch.uint8, device=self.device)
+        rc = self._lib.gcmc_run_moves_micro(self._h, seed, first_move, n_moves, C.byref(cm), C.byref(st),
+                                            _ptr(tb) if trace else None)
+        if check_status:
+            check(rc, self._h, "gcmc_run_moves_micro")
+        stats = stats_dict(st, self.S)
+        stats["status"] = rc
+        if trace:
+            return stats, tb[:n_moves].cpu().numpy().copy().view(TRACE_DTYPE).reshape(-1)
+        return stats
+
     def get_state(self):
         n = self.counts()
         N = int(n.sum())

@@ -67,6 +67,8 @@ def _args():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the cutoff sweep figures")
+    ap.add_argument("--micro-only", action="store_true",
+                    help="only the microcell chain's single-chain rates (moves per chain: --moves, default 10^5)")
     ap.add_argument("--sweep-moves", type=int, default=100_000, help="moves per cutoff and precision")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the throughput kernels (trial energies, total energy, gradient, cell build)")
@@ -516,6 +518,24 @@ def main():
         dev = torch.device("cuda", local)
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
         print(json.dumps({"kernels": _kernel_figures(dev, flush, None)}))
+        return 0
+    if a.micro_only:
+        from paper_1408_3764_gb300 import workloads as W
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        M = a.moves or 100_000
+        out = {}
+        if a.workload == "c2":  # one workload: the 131,072-particle chain in the given precision
+            prec = a.precision or "fp32"
+            out["c2_131072_" + prec] = _micro_chain_rate(W.c2_fp32_vs_fp64(), prec, M, dev, flush)
+        else:
+            out["c1_2048_fp64"] = _micro_chain_rate(W.c1_plain_fp64(), "fp64", M, dev, flush)
+            for prec in ("fp32", "fp64"):
+                out["c2_131072_" + prec] = _micro_chain_rate(W.c2_fp32_vs_fp64(), prec, M, dev, flush)
+            for rc in (2.5, 4.25):
+                out["sweep_87296_rc%.2f_fp32" % rc] = _micro_chain_rate(W.cutoff_sweep(rc), "fp32", M, dev, flush)
+        print(json.dumps({"micro": out}))
         return 0
     chains = _chains(a.workload)
     # the CPU baseline's worker processes are spawned before the first GPU call

@@ -114,7 +114,12 @@ void micro_free(gcmc_ctx *ctx)
     ctx->mc_valid = false;
 }
 
-static size_t micro_smem(int64_t ncm) { return (size_t)((ncm + 1) / 2 + 15) / 16 * 16; }
+// dynamic shared memory of the chain: the cube's cell offsets (4 bytes per
+// cell of the cube) and the microcell counts (4 bits per microcell)
+static size_t micro_smem(int64_t ncm, int nax)
+{
+    return (size_t)nax * nax * nax * 4 + (size_t)((ncm + 1) / 2 + 15) / 16 * 16;
+}
 
 struct MicroShared;  // defined with the chain kernel below
 static size_t micro_static_smem();
@@ -126,7 +131,8 @@ gcmc_status micro_build(gcmc_ctx *ctx, double edge, int cap_req)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_build_microcells: more than 1023 microcells per side");
     const int M = (int)md;
     const int64_t ncm = (int64_t)M * M * M;
-    if (micro_smem(ncm) + micro_static_smem() + 1024 > ctx->smem_optin)
+    const int D = 1 + (int)(((uint64_t)(ctx->rcg - 1) * (uint64_t)M) >> 32);
+    if (micro_smem(ncm, std::min(2 * D + 1, M)) + micro_static_smem() + 1024 > ctx->smem_optin)
         return fail(ctx, GCMC_ERR_INVALID_ARG,
                     "gcmc_build_microcells: too many microcells for the chain's on-chip counters");
     SpeciesPrefix p{};
@@ -168,7 +174,7 @@ gcmc_status micro_build(gcmc_ctx *ctx, double edge, int cap_req)
     ctx->mc_M = M;
     ctx->mc_ncell = ncm;
     ctx->mc_cap = cap;
-    ctx->mc_D = 1 + (int)(((uint64_t)(ctx->rcg - 1) * (uint64_t)M) >> 32);
+    ctx->mc_D = D;
     ctx->mc_valid = true;
     return GCMC_OK;
 }
@@ -263,51 +269,75 @@ struct MTrial {
 
 // Sum over the cube(s) of one trial: sign -1 for the old position, +1 for
 // the new one; the particle's own record is skipped by its tag.
-template <bool F64>
-__device__ __forceinline__ void micro_sum(const MicroArgs &a, const uint8_t *nb, const MTrial &t, double &e64,
-                                          double &u64, float &e32, float &u32)
+// Cube origin (cell coordinates of its lowest corner, or 0 when the cube
+// spans the whole axis) of the cube around grid point P.
+__device__ __forceinline__ int3 cube_base(const MicroArgs &a, uint4 P)
 {
-    const int nax = a.nax, n3 = nax * nax * nax;
-    const int sides = (t.type == 0) ? 2 : 1;
-    for (int f = threadIdx.x; f < sides * n3; f += kMicroThreads) {
-        const int side = f >= n3;  // 0: first cube, 1: second (displacement's new position)
-        const int g = f - side * n3;
-        const bool old_side = (t.type == 2) || (t.type == 0 && side == 0);
-        const uint4 P = old_side ? t.Po : t.Pn;
-        const int ox = g % nax, oy = (g / nax) % nax, oz = g / (nax * nax);
-        const int M = (int)a.M;
-        int bx = 0, by = 0, bz = 0;
-        if (nax < M) {
-            bx = cell_coord(P.x, a.M) - a.D;
-            by = cell_coord(P.y, a.M) - a.D;
-            bz = cell_coord(P.z, a.M) - a.D;
+    if (a.nax >= (int)a.M) return make_int3(0, 0, 0);
+    return make_int3(cell_coord(P.x, a.M) - a.D, cell_coord(P.y, a.M) - a.D, cell_coord(P.z, a.M) - a.D);
+}
+
+__device__ __forceinline__ int wrapm(int x, int M) { return x < 0 ? x + M : (x >= M ? x - M : x); }
+
+template <bool F64>
+__device__ __forceinline__ void micro_sum(const MicroArgs &a, const uint8_t *nb, const uint32_t *cube_off,
+                                          const MTrial &t, double &e64, double &u64, float &e32, float &u32)
+{
+    constexpr int kB = 4;  // cells a thread takes per pass: their slot loads issue together
+    const int nax = a.nax, n3 = nax * nax * nax, M = (int)a.M;
+    const int total = ((t.type == 0) ? 2 : 1) * n3;
+    const int sp = t.s;
+    // the first cube is around the old position (displacement, deletion) or
+    // the new one (insertion); the second (displacement) around the new one
+    const uint4 P0 = (t.type == 1) ? t.Pn : t.Po;
+    const int3 b0 = cube_base(a, P0), b1 = cube_base(a, t.Pn);
+    for (int f0 = threadIdx.x; f0 < total; f0 += kB * kMicroThreads) {
+        int64_t c[kB];
+        int cnt[kB];
+        bool old_side[kB];
+        int kmax = 0;
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+            const int f = f0 + j * kMicroThreads;
+            c[j] = 0;
+            cnt[j] = 0;
+            old_side[j] = true;
+            if (f < total) {
+                const int side = f >= n3;
+                const uint32_t o = cube_off[f - side * n3];  // ox | oy << 10 | oz << 20
+                old_side[j] = (t.type == 2) || (t.type == 0 && side == 0);
+                const int3 b = side ? b1 : b0;
+                const int cx = wrapm(b.x + (int)(o & 1023u), M);
+                const int cy = wrapm(b.y + (int)((o >> 10) & 1023u), M);
+                const int cz = wrapm(b.z + (int)(o >> 20), M);
+                c[j] = ((int64_t)cz * M + cy) * M + cx;
+                cnt[j] = nib_get(nb, c[j]);
+                kmax = max(kmax, cnt[j]);
+            }
         }
-        int cx = bx + ox, cy = by + oy, cz = bz + oz;
-        cx += cx < 0 ? M : 0;
-        cx -= cx >= M ? M : 0;
-        cy += cy < 0 ? M : 0;
-        cy -= cy >= M ? M : 0;
-        cz += cz < 0 ? M : 0;
-        cz -= cz >= M ? M : 0;
-        const int64_t c = ((int64_t)cz * M + cy) * M + cx;
-        const int cnt = nib_get(nb, c);
-        const int sp = t.s;
-        for (int k = 0; k < cnt; ++k) {
-            const uint4 q = a.mc_pos[(int64_t)k * a.ncm + c];
-            if (t.type != 1 && q.w == t.Po.w) continue;
-            const GridSep sep = grid_sep(P, q);
-            if (sep.g >= a.R2) continue;
-            const int kk = sp * kMaxSpecies + (int)tag_species(q.w);
-            if constexpr (F64) {
-                double u, m;
-                lj_f64(sep, a.fd.c4e[kk], a.fd.sig2[kk], u, m);
-                e64 += old_side ? -u : u;
-                u64 += m;
-            } else {
-                float u, m;
-                lj_f32(sep, a.ff.c4e[kk], a.ff.sig2[kk], u, m);
-                e32 += old_side ? -u : u;
-                u32 += m;
+        for (int k = 0; k < kmax; ++k) {
+            uint4 q[kB];
+#pragma unroll
+            for (int j = 0; j < kB; ++j)
+                if (k < cnt[j]) q[j] = a.mc_pos[(int64_t)k * a.ncm + c[j]];
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                if (k >= cnt[j]) continue;
+                if (t.type != 1 && q[j].w == t.Po.w) continue;
+                const GridSep sep = grid_sep(old_side[j] ? t.Po : t.Pn, q[j]);
+                if (sep.g >= a.R2) continue;
+                const int kk = sp * kMaxSpecies + (int)tag_species(q[j].w);
+                if constexpr (F64) {
+                    double u, m;
+                    lj_f64(sep, a.fd.c4e[kk], a.fd.sig2[kk], u, m);
+                    e64 += old_side[j] ? -u : u;
+                    u64 += m;
+                } else {
+                    float u, m;
+                    lj_f32(sep, a.ff.c4e[kk], a.ff.sig2[kk], u, m);
+                    e32 += old_side[j] ? -u : u;
+                    u32 += m;
+                }
             }
         }
     }
@@ -316,9 +346,16 @@ __device__ __forceinline__ void micro_sum(const MicroArgs &a, const uint8_t *nb,
 template <bool F32>
 __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArgs a)
 {
-    extern __shared__ __align__(16) uint8_t nb[];  // microcell counts, 4 bits each
+    // dynamic shared memory: the cube's cell offsets, then the microcell counts (4 bits each)
+    extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ MicroShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n3 = a.nax * a.nax * a.nax;
+    uint32_t *cube_off = (uint32_t *)dyn;
+    uint8_t *nb = dyn + (size_t)n3 * 4;
+    for (int g = tid; g < n3; g += kMicroThreads)
+        cube_off[g] = (uint32_t)(g % a.nax) | ((uint32_t)((g / a.nax) % a.nax) << 10) |
+                      ((uint32_t)(g / (a.nax * a.nax)) << 20);
     for (int64_t c = tid; c < (a.ncm + 1) / 2; c += kMicroThreads) {
         const int lo = a.mc_count[2 * c];
         const int hi = (2 * c + 1 < a.ncm) ? a.mc_count[2 * c + 1] : 0;
@@ -396,7 +433,7 @@ __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArg
         if (t.possible) {
             if constexpr (F32) {
                 const int buf = (ev32++) & 1;
-                micro_sum<false>(a, nb, t, de, da, e32, u32);
+                micro_sum<false>(a, nb, cube_off, t, de, da, e32, u32);
                 e32 = warp_sum(e32);
                 u32 = warp_sum(u32);
                 if (lane == 0) {
@@ -431,7 +468,7 @@ __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArg
             }
             if (!F32 || refined < 0) {
                 double e64 = 0.0, u64 = 0.0;
-                micro_sum<true>(a, nb, t, e64, u64, e32, u32);
+                micro_sum<true>(a, nb, cube_off, t, e64, u64, e32, u32);
                 e64 = warp_sum(e64);
                 u64 = warp_sum(u64);
                 const int buf = (ev64++) & 1;
@@ -534,44 +571,61 @@ __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArg
                     if (t.type == 1) sh.n[sp] = ns + 1;
                     else if (t.type == 2) sh.n[sp] = ns - 1;
                 }
-            } else if (warp == 1 && lane == 0) {
-                // microcells: append, remove by swap-with-last, retag the refilled index
+            } else if (warp == 1) {
+                // microcells: append, remove by swap-with-last, retag the refilled index.
+                // The lanes read a cell's slots at once (at most 15): the slot holding
+                // `tag` (-1 if none) and the cell's last record.
                 const int64_t ncm = a.ncm;
-                auto find = [&](int64_t c, uint32_t tag) {
+                auto scan = [&](int64_t c, uint32_t tag, int &slot, uint4 &lastv) {
                     const int n = nib_get(nb, c);
-                    for (int k = 0; k < n; ++k)
-                        if (a.mc_pos[(int64_t)k * ncm + c].w == tag) return k;
-                    return -1;
-                };
-                auto remove = [&](int64_t c, int k) {
-                    const int n = nib_get(nb, c);
-                    if (k != n - 1) a.mc_pos[(int64_t)k * ncm + c] = a.mc_pos[(int64_t)(n - 1) * ncm + c];
-                    nib_set(nb, c, n - 1);
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (lane < n) v = a.mc_pos[(int64_t)lane * ncm + c];
+                    const unsigned b = __ballot_sync(0xffffffffu, lane < n && v.w == tag);
+                    slot = b ? __ffs(b) - 1 : -1;
+                    const int src = max(n - 1, 0);
+                    lastv.x = __shfl_sync(0xffffffffu, v.x, src);
+                    lastv.y = __shfl_sync(0xffffffffu, v.y, src);
+                    lastv.z = __shfl_sync(0xffffffffu, v.z, src);
+                    lastv.w = __shfl_sync(0xffffffffu, v.w, src);
                 };
                 auto append = [&](int64_t c, uint4 v) {
                     const int n = nib_get(nb, c);
                     a.mc_pos[(int64_t)n * ncm + c] = v;
                     nib_set(nb, c, n + 1);
                 };
-                const int k = t.type != 1 ? find(mo, t.Po.w) : 0;
-                if (k < 0) {
-                    sh.err = kStatusBadInput;
-                } else if (t.type == 0) {
-                    if (mn == mo) {
-                        a.mc_pos[(int64_t)k * ncm + mo] = t.Pn;
-                    } else {
-                        remove(mo, k);
+                auto remove = [&](int64_t c, int k, uint4 lastv) {
+                    const int n = nib_get(nb, c);
+                    if (k != n - 1) a.mc_pos[(int64_t)k * ncm + c] = lastv;
+                    nib_set(nb, c, n - 1);
+                };
+                int k = 0;
+                uint4 lastv = make_uint4(0, 0, 0, 0);
+                if (t.type != 1) scan(mo, t.Po.w, k, lastv);
+                if (lane == 0) {
+                    if (k < 0) {
+                        sh.err = kStatusBadInput;
+                    } else if (t.type == 0) {
+                        if (mn == mo) {
+                            a.mc_pos[(int64_t)k * ncm + mo] = t.Pn;
+                        } else {
+                            remove(mo, k, lastv);
+                            append(mn, t.Pn);
+                        }
+                    } else if (t.type == 1) {
                         append(mn, t.Pn);
+                    } else {
+                        remove(mo, k, lastv);
                     }
-                } else if (t.type == 1) {
-                    append(mn, t.Pn);
-                } else {
-                    remove(mo, k);
-                    const long long last = ns - 1;
-                    if (t.idx != last) {
-                        const uint4 Q = a.pos_by_id[sb + last];
-                        const int64_t mq = micro_of(Q, a.M);
-                        const int kq = find(mq, Q.w);
+                }
+                __syncwarp();
+                const long long last = ns - 1;
+                if (t.type == 2 && k >= 0 && t.idx != last) {
+                    const uint4 Q = a.pos_by_id[sb + last];
+                    const int64_t mq = micro_of(Q, a.M);
+                    int kq;
+                    uint4 unused;
+                    scan(mq, Q.w, kq, unused);
+                    if (lane == 0) {
                         if (kq < 0) sh.err = kStatusBadInput;
                         else a.mc_pos[(int64_t)kq * ncm + mq].w = make_tag((uint32_t)t.idx, (uint32_t)sp);
                     }
@@ -660,7 +714,7 @@ gcmc_status run_moves_micro(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_
     ctx->last_refines = 0;
     MicroOut *d_out = nullptr;
     GCMC_CUDA(ctx, cudaMalloc(&d_out, sizeof(MicroOut)));
-    const size_t smem = micro_smem(ctx->mc_ncell);
+    const size_t smem = micro_smem(ctx->mc_ncell, std::min(2 * ctx->mc_D + 1, ctx->mc_M));
     auto kern = ctx->precision == GCMC_FP32 ? k_micro_chain<true> : k_micro_chain<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t done = 0;

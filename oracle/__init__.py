@@ -82,6 +82,12 @@ def lib():
         L.orc_micro_state.restype = i64
         L.orc_micro_per_side.argtypes = [vp]
         L.orc_micro_per_side.restype = C.c_int
+        L.orc_micro_cube.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.orc_micro_cube.restype = i64
+        L.orc_energy_micro.argtypes = [vp, vp, C.c_int, C.c_int, i64, C.c_int, vp]
+        L.orc_energy_micro.restype = d
+        L.orc_energy_brute.argtypes = [vp, vp, C.c_int, C.c_int, i64, vp]
+        L.orc_energy_brute.restype = d
         _lib = L
     return _lib
 
@@ -294,6 +300,31 @@ class System:
         if M < 0:
             raise ValueError("bad microcell edge")
         return M
+
+    def micro_cube(self, centre, D: int) -> np.ndarray:
+        """Microcell ids of the cube of half-width D around microcell `centre`
+        (x, y, z), in thread order (x fastest), Sec. 3.3.2."""
+        M = lib().orc_micro_per_side(self._h)
+        n = min(2 * D + 1, M)
+        out = np.zeros(n ** 3, np.int64)
+        k = lib().orc_micro_cube(self._h, int(centre[0]), int(centre[1]), int(centre[2]), int(D), _p(out))
+        return out[:k]
+
+    def energy_micro(self, P_grid, species: int, exclude=(-1, -1), D: int = 3):
+        """(energy, uabs) of a particle at grid position P_grid summed over the
+        cube of microcells around it."""
+        P = np.ascontiguousarray(np.asarray(P_grid, dtype=np.uint32).reshape(3))
+        ua = np.zeros(1, np.float64)
+        e = lib().orc_energy_micro(self._h, _p(P), int(species), int(exclude[0]), int(exclude[1]), int(D), _p(ua))
+        return e, float(ua[0])
+
+    def energy_brute_grid(self, P_grid, species: int, exclude=(-1, -1)):
+        """(energy, uabs) of a particle at grid position P_grid against every
+        particle but `exclude` (the definition)."""
+        P = np.ascontiguousarray(np.asarray(P_grid, dtype=np.uint32).reshape(3))
+        ua = np.zeros(1, np.float64)
+        e = lib().orc_energy_brute(self._h, _p(P), int(species), int(exclude[0]), int(exclude[1]), _p(ua))
+        return e, float(ua[0])
 
     def micro_state(self):
         """(M, per-microcell counts, concatenated per-cell lists of (i << 8) | s,

@@ -378,6 +378,60 @@ int64_t orc_micro_state(const orc_sys *sys, int64_t *counts, uint32_t *refs)
 
 int orc_micro_per_side(const orc_sys *sys) { return sys->mc_M; }
 
+static double pair_energy(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3], int tb,
+                          double *uabs);
+
+/* The cube of microcells around microcell (cx, cy, cz), Sec. 3.3.2: thread
+ * (tx, ty, tz) of an n x n x n cube, n = 2D + 1, takes the microcell at
+ * offset (tx - D, ty - D, tz - D), wrapped around the periodic box.  When
+ * n exceeds M the axis is taken whole, each cell once (offsets 0 .. M-1
+ * from cell 0).  Writes the cells in thread order, x fastest; returns the
+ * count (n_x n_y n_z). */
+int64_t orc_micro_cube(const orc_sys *sys, int cx, int cy, int cz, int D, int64_t *cells)
+{
+    int M = sys->mc_M;
+    int n = 2 * D + 1;
+    int full = n > M;
+    if (full) n = M;
+    int64_t k = 0;
+    for (int tz = 0; tz < n; ++tz)
+        for (int ty = 0; ty < n; ++ty)
+            for (int tx = 0; tx < n; ++tx) {
+                int x = full ? tx : cx - D + tx;
+                int y = full ? ty : cy - D + ty;
+                int z = full ? tz : cz - D + tz;
+                x = ((x % M) + M) % M;
+                y = ((y % M) + M) % M;
+                z = ((z % M) + M) % M;
+                cells[k++] = ((int64_t)z * M + y) * M + x;
+            }
+    return k;
+}
+
+/* Energy of a particle of species t at P with every listed particle in the
+ * cube of microcells (half-width D) around P's microcell, skipping particle
+ * (excl_s, excl_i); adds |rep| + |att| to *uabs when given.  With a cube
+ * that covers the cutoff this is the brute-force sum over all particles. */
+double orc_energy_micro(const orc_sys *sys, const uint32_t P[3], int t, int excl_s, int64_t excl_i, int D,
+                        double *uabs)
+{
+    int M = sys->mc_M;
+    int64_t n = (int64_t)(2 * D + 1 < M ? 2 * D + 1 : M);
+    int64_t *cells = (int64_t *)malloc((size_t)(n * n * n) * sizeof(int64_t));
+    int64_t nc = orc_micro_cube(sys, cell_coord(P[0], M), cell_coord(P[1], M), cell_coord(P[2], M), D, cells);
+    double e = 0.0;
+    for (int64_t k = 0; k < nc; ++k) {
+        int64_t c = cells[k];
+        for (int64_t j = 0; j < sys->mc_len[c]; ++j) {
+            orc_ref r = sys->mc[c][j];
+            if (r.s == excl_s && r.i == excl_i) continue;
+            e += pair_energy(sys, P, t, &sys->pos[r.s][3 * r.i], r.s, uabs);
+        }
+    }
+    free(cells);
+    return e;
+}
+
 /* Binning, Sec. 3.2.1.  Particles keep the order in which they are given:
  * the index of a particle within its species is its rank among the input
  * particles of that species, and every cell lists its particles in input

@@ -11,8 +11,11 @@ their upkeep over a chain, and the cube of microcells that covers the cutoff.
 * Cube: every pair within the cutoff lies within D microcells of each other
   along each axis (minimum image), D = 1 + floor((rcg - 1) M / 2^32), rcg the
   smallest integer with rcg^2 >= R2 -- the half-width of the cube of
-  microcells the GPU evaluates.
+  microcells the GPU evaluates; the paper's mapping example of threads to
+  microcells (Sec. 3.3.2, tests/golden/microcell_mapping.txt); a particle's
+  energy summed over its cube equals the brute-force sum over all particles.
 """
+import os
 import math
 from fractions import Fraction
 
@@ -128,3 +131,53 @@ def test_micro_cube_covers_the_cutoff(n, L, rc, edge):
         assert (dc <= D).all()
     # the bound is attained or one cell short of it (it is not loose)
     assert worst >= min(D, M // 2) - 1
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cube_half_width(o, M):
+    rcg = math.isqrt(o.R2 - 1) + 1
+    return 1 + ((rcg - 1) * M >> 32)
+
+
+def test_microcell_mapping_example():
+    rows = [list(map(int, ln.split())) for ln in open(os.path.join(GOLDEN, "microcell_mapping.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    o = O.System(20.0, 2.5, [[1.0]], [[1.0]])
+    o.build(np.zeros((0, 3)), np.zeros(0, np.int32))
+    M = o.micro_build(1.0)
+    assert M == 20
+    D = _cube_half_width(o, M)
+    for cx, cy, cz, n, tx, ty, tz, x, y, z in rows:
+        assert 2 * D + 1 == n  # a 2.5 sigma cutoff needs the 7 x 7 x 7 cube
+        cube = o.micro_cube((cx, cy, cz), D)
+        assert len(cube) == n ** 3 == 343
+        c = int(cube[tx + n * ty + n * n * tz])
+        assert (c % M, (c // M) % M, c // (M * M)) == (x, y, z)
+    # a 2.75 sigma cutoff needs the same cube
+    o2 = O.System(20.0, 2.75, [[1.0]], [[1.0]])
+    o2.build(np.zeros((0, 3)), np.zeros(0, np.int32))
+    assert 2 * _cube_half_width(o2, o2.micro_build(1.0)) + 1 == 7
+
+
+@pytest.mark.parametrize("n,L,rc,S", [(900, 11.0, 2.5, 2), (1200, 12.5, 3.75, 1),
+                                      (150, 6.3, 3.0, 1)])
+def test_micro_cube_energy_equals_brute_force(n, L, rc, S):
+    pos, types, eps, sigma = W.tiny_system(n=n, L=L, rc=rc, n_species=S, seed=n + 3)
+    o = O.System(L, rc, eps, sigma)
+    o.build(pos, types)
+    M = o.micro_build(1.0)
+    D = _cube_half_width(o, M)
+    cnt, X, _, _ = o.state()
+    ids = [(s, i) for s in range(S) for i in range(cnt[s])]
+    rng = np.random.default_rng(n)
+    for r in rng.choice(len(ids), size=min(60, len(ids)), replace=False):
+        s, i = ids[r]
+        e_m, u_m = o.energy_micro(X[r], s, (s, i), D)
+        e_b, u_b = o.energy_brute_grid(X[r], s, (s, i))
+        assert e_m == pytest.approx(e_b, rel=1e-13, abs=1e-13 * u_b) and u_m == pytest.approx(u_b, rel=1e-13)
+    for P in rng.integers(0, 2 ** 32, size=(40, 3), dtype=np.uint64).astype(np.uint32):
+        e_m, u_m = o.energy_micro(P, 0, (-1, -1), D)
+        e_b, u_b = o.energy_brute_grid(P, 0, (-1, -1))
+        assert e_m == pytest.approx(e_b, rel=1e-13, abs=1e-13 * u_b) and u_m == pytest.approx(u_b, rel=1e-13)

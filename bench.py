@@ -272,16 +272,25 @@ def run_reference(a):
 # ------------------------------------------------------------- GPU side ---
 
 class Runner:
-    """The chains of one workload on the GPU, and one step of the hot path."""
+    """The chains of one workload on the GPU, and one step of the hot path.
+
+    Every box has its own CUDA stream; the per-box steps before and after the
+    batched chain (cell build, full-system energy, gradient) are issued from a
+    small pool of host threads, so that their host round trips overlap."""
 
     def __init__(self, chains, precision, dev, rank, host_inputs=False, virial=False):
+        import concurrent.futures
         import torch
         from paper_1408_3764_gb300.gcmc import Batch, Box, Mix
         self.torch = torch
         self.chains = chains
         self.dev = dev
         self.stream = torch.cuda.current_stream(dev)
-        self.boxes = [Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev) for w in chains]
+        self.box_streams = [torch.cuda.Stream(device=dev) for _ in chains]
+        self.boxes = [Box(w.L, w.rc, w.eps, w.sigma, precision=precision, device=dev, stream=s)
+                      for w, s in zip(chains, self.box_streams)]
+        self.pool = (concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(chains)))
+                     if len(chains) > 1 else None)
         self.mixes = [Mix(w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z, virial=virial) for w in chains]
         self.seeds = [w.seed + 7919 * rank for w in chains]  # replicas: independent chains per rank
         self.batch = Batch(self.boxes) if len(chains) > 1 else None
@@ -296,34 +305,54 @@ class Runner:
         n = sum(b.launches() for b in self.boxes)
         return n + (self.batch.launches() if self.batch else 0)
 
+    def _map(self, fn):
+        if self.pool is None:
+            return [fn(i) for i in range(len(self.boxes))]
+        return list(self.pool.map(fn, range(len(self.boxes))))
+
+    def _prepare(self, i):
+        """Box i: inputs (copied from pinned host memory in the e2e runner),
+        cell build and full-system energy, on the box's stream."""
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        with torch.cuda.stream(self.box_streams[i]):
+            if self.host_inputs:
+                pos = self.pos_h[i].to(self.dev, non_blocking=True)
+                typ = self.typ_h[i].to(self.dev, non_blocking=True)
+            else:
+                pos, typ = self.pos_d[i], self.typ_d[i]
+            b = self.boxes[i]
+            b.build_cells(pos, typ)
+            return b.total_energy()
+
+    def _gradient(self, i):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        with torch.cuda.stream(self.box_streams[i]):
+            return self.boxes[i].energy_grad(want_pos=True)
+
     def step(self, k, M):
         torch = self.torch
-        if self.host_inputs:
-            pos = [p.to(self.dev, non_blocking=True) for p in self.pos_h]
-            typ = [t.to(self.dev, non_blocking=True) for t in self.typ_h]
-        else:
-            pos, typ = self.pos_d, self.typ_d
-        energies = []
-        for i, b in enumerate(self.boxes):
-            b.build_cells(pos[i], typ[i])
-            energies.append(b.total_energy())
+        energies = self._map(self._prepare)
         if self.batch is None:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(self.stream)
+            e0.record(self.box_streams[0])  # the chain runs on the box's stream
             stats = [self.boxes[0].run_moves(self.seeds[0], k * M, M, self.mixes[0])]
-            e1.record(self.stream)
+            e1.record(self.box_streams[0])
             e1.synchronize()
             self.chain_ms = e0.elapsed_time(e1)
         else:
             stats = self.batch.run_moves(self.seeds, k * M, M, self.mixes)
             self.chain_ms = self.batch.device_ms()
-        grads = [b.energy_grad(want_pos=True) for b in self.boxes]
+        grads = self._map(self._gradient)
         return stats, grads, energies
 
     def close(self):
         if self.batch:
             self.batch.close()
+        if self.pool is not None:
+            self.pool.shutdown()
 
 
 def _time_steps(runner, first_step, steps, M, flush):
@@ -335,6 +364,7 @@ def _time_steps(runner, first_step, steps, M, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(runner.stream)
+        runner.stream.synchronize()  # the flush is done before any box stream starts
         last = runner.step(first_step + k, M)
         e1.record(runner.stream)
         e1.synchronize()

@@ -106,6 +106,8 @@ typedef struct {
     int64_t n[GCMC_MAX_SPECIES]; /* particles per species after the last move */
     double virial;         /* running virial after the last move (GCMC_MIX_VIRIAL; else NaN) */
     double sum_virial;     /* sum over the moves of the running virial after the move */
+    double chain_ms;       /* device time of the chain's CTA, start to finish, summed over the
+                            * call's launches (global timer; 0 for the microcell chain) */
 } gcmc_move_stats;
 
 /* One record per move of gcmc_run_moves (32 bytes). */

@@ -40,7 +40,7 @@ class MoveStats(C.Structure):
     _fields_ = [("attempted", C.c_int64 * 3), ("accepted", C.c_int64 * 3), ("flagged", C.c_int64),
                 ("moves_done", C.c_int64), ("energy", C.c_double), ("sum_energy", C.c_double),
                 ("sum_n", C.c_double), ("n", C.c_int64 * MAX_SPECIES), ("virial", C.c_double),
-                ("sum_virial", C.c_double)]
+                ("sum_virial", C.c_double), ("chain_ms", C.c_double)]
 
 
 class Geometry(C.Structure):

@@ -381,11 +381,11 @@ gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species
         ctx->launches += 2;
         GCMC_CUDA(ctx, cudaGetLastError());
     }
-    int64_t nn[kMaxSpecies] = {0};
-    for (int s = 0; s < S; ++s) nn[s] = hsmall[s];
-    GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_n, nn, sizeof(nn), cudaMemcpyHostToDevice, st));
-    GCMC_CUDA(ctx, cudaStreamSynchronize(st));
-    for (int s = 0; s < kMaxSpecies; ++s) ctx->n_host[s] = nn[s];
+    // the per-species counts go to the device from the device (stream-ordered,
+    // no host round trip)
+    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_n, 0, kMaxSpecies * sizeof(int64_t), st));
+    GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_n, small, (size_t)S * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    for (int s = 0; s < kMaxSpecies; ++s) ctx->n_host[s] = s < S ? hsmall[s] : 0;
     ctx->n_build = n;
     ctx->built = true;
     ctx->compact_valid = true;

@@ -59,6 +59,7 @@ struct ChainOut {
     long long refines;      // trials decided in FP64 after the FP32 band test
     double virial;          // running virial after the last move (virial runs)
     double sum_virial;      // sum over the moves of the running virial
+    unsigned long long t0, t1;  // global timer (ns) when the chain's CTA started and finished
 };
 
 struct ChainArgs {
@@ -956,6 +957,8 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
     constexpr int NTH = (EW + 2) * 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     uint16_t *cnt = (uint16_t *)dyn;
+    unsigned long long t_start = 0;
+    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     __shared__ Shared sh;
     __shared__ TeamCtl ctl[NTEAM];
     __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
@@ -1425,6 +1428,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         if (!(o.energy - o.energy == 0.0)) st |= kStatusNonFinite;
         o.status = st;
         o.pad = sh.where;
+        unsigned long long t_end;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        o.t0 = t_start;
+        o.t1 = t_end;
     }
 }
 
@@ -1664,6 +1671,7 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
             j.agg.moves_done += o.moves_done;
             j.agg.sum_energy += o.sum_energy;
             j.agg.sum_n += o.sum_n;
+            j.agg.chain_ms += (double)(o.t1 - o.t0) * 1e-6;
             j.agg.energy = o.energy;
             if (j.mix.flags & GCMC_MIX_VIRIAL) {
                 j.agg.virial = o.virial;

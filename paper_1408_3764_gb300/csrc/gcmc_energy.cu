@@ -473,15 +473,17 @@ gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
     const double e = ew[0];
     ctx->virial = ew[1];
     ctx->virial_valid = true;
+    // the running values on the device come from the device (no second host round trip)
+    const double *dsum = ctx->d_red + 2 * ctx->ncell;
     if (virial_only) {
-        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy + 1, &ctx->virial, sizeof(double), cudaMemcpyHostToDevice,
+        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy + 1, dsum + 1, sizeof(double), cudaMemcpyDeviceToDevice,
                                        ctx->stream));
     } else {
         ctx->energy = e;
         ctx->energy_valid = true;
-        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, ew, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, dsum, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
     }
-    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (energy) *energy = e;
     return GCMC_OK;
 }

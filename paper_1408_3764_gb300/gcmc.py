@@ -58,7 +58,7 @@ def stats_dict(st: MoveStats, n_species: int) -> dict:
                 moves_done=int(st.moves_done), energy=float(st.energy),
                 sum_energy=float(st.sum_energy), sum_n=float(st.sum_n),
                 n=[int(st.n[s]) for s in range(n_species)], virial=float(st.virial),
-                sum_virial=float(st.sum_virial))
+                sum_virial=float(st.sum_virial), chain_ms=float(st.chain_ms))
 
 
 class Box:

@@ -167,6 +167,12 @@ struct AxisList {
     int n;
 };
 
+__device__ __forceinline__ bool near1(int d, int T)
+{
+    d = d < 0 ? -d : d;
+    return d <= 1 || d == T - 1;
+}
+
 __device__ __forceinline__ int wrapc(int x, int T) { return x < 0 ? x + T : (x >= T ? x - T : x); }
 
 template <typename V>
@@ -204,18 +210,6 @@ __device__ __forceinline__ AxisList axis_list(int p, int q, int cross, uint32_t 
     return L;
 }
 
-__device__ __forceinline__ bool near1(int d, int T)
-{
-    d = d < 0 ? -d : d;
-    return d <= 1 || d == T - 1;
-}
-
-__device__ __forceinline__ bool in_work(const Trial &t, int x, int y, int z, int T)
-{
-    if (!t.possible) return false;
-    if (near1(x - (int)t.px, T) && near1(y - (int)t.py, T) && near1(z - (int)t.pz, T)) return true;
-    return t.cross && near1(x - (int)t.qx, T) && near1(y - (int)t.qy, T) && near1(z - (int)t.qz, T);
-}
 
 // ---------------------------------------------------------------- shared state
 struct WordRec {
@@ -238,16 +232,18 @@ struct Slot {  // evaluators -> committer, one per move in flight
     int c0;                       // moves committed when the evaluation started
     int arrive;                   // warps finished
     int tag;                      // move + 1 of the evaluation under way, 0 none
+    int pseq[kGMax];              // per warp: count epoch its work-cell counts were read in (-1 torn)
     int pad[2];
 };
 
 struct LogRec {  // committer -> evaluation validity
     int flags;         // bit0 accepted, bit1 N changed
     int mx[3], my[3], mz[3];  // cells written (-1 none)
-    int cchg[3];       // 1: that cell's count changed (append or removal)
     int ids[3];        // (s << 24) | index of records written
     int np;            // positions that gained or lost a particle
+    int has_moved;     // a removal moved the cell's last entry into the freed slot
     uint4 pos[2];
+    uint4 moved;       // that entry
 };
 
 struct BookRec {  // committer -> keeper
@@ -281,6 +277,12 @@ struct __align__(16) Shared {
     int stop;       // the committer stopped: no further moves are taken
     int status;
     int where;      // which waits gave up: 1 team leader, 2 committer, 4 keeper
+    // count epoch: even while no cell count is being changed, bumped before
+    // and after every change of the counts (a sequence lock)
+    int seq;
+    // 1 while this chain accepts most of its insertions [0] / deletions [1]
+    // (the bet the count prediction makes on moves not yet evaluated)
+    int likely[2];
 };
 
 __device__ __forceinline__ int vload(const int &x) { return *(volatile const int *)&x; }
@@ -585,6 +587,7 @@ struct Chain {
         float e, ua, w;
         double de, da, dw;
         int self_slot, has_last;
+        int seq;  // count epoch of the work-cell counts this warp read, -1 if a change tore them
         uint4 last;
     };
 
@@ -623,17 +626,20 @@ struct Chain {
             Y = axis_list(t.py, t.qy, 1, kOld, T);
             Z = axis_list(t.pz, t.qz, 1, kOld, T);
         }
-        // a lane owns work cells lane and lane + 32
+        // a lane owns work cells lane and lane + 32; their counts are read
+        // inside one count epoch (the sequence lock around count changes)
         int ca = 0, cb = 0, na = 0, nb = 0;
         uint32_t fa = 0, fb = 0;
-        if (lane < nw) {
-            work_cell(t, X, Y, Z, lane, ca, fa);
-            na = fa ? (int)cnt[ca] : 0;
-        }
-        if (lane + 32 < nw) {
-            work_cell(t, X, Y, Z, lane + 32, cb, fb);
-            nb = fb ? (int)cnt[cb] : 0;
-        }
+        if (lane < nw) work_cell(t, X, Y, Z, lane, ca, fa);
+        if (lane + 32 < nw) work_cell(t, X, Y, Z, lane + 32, cb, fb);
+        const int s0 = vload(sh.seq);
+        __threadfence_block();
+        if (lane < nw) na = fa ? (int)cnt[ca] : 0;
+        if (lane + 32 < nw) nb = fb ? (int)cnt[cb] : 0;
+        __threadfence_block();
+        const int s1 = vload(sh.seq);
+        const int w0 = __shfl_sync(0xffffffffu, s0, 0);
+        o.seq = __all_sync(0xffffffffu, s0 == s1 && s0 == w0 && !(s0 & 1)) ? w0 : -1;
         // items end at ia (cells 0 .. 31) and ib (cells 32 .. 63), inclusive
         const int ia = warp_inclusive_scan(na);
         const int ib = warp_inclusive_scan(nb) + __shfl_sync(0xffffffffu, ia, 31);
@@ -733,12 +739,20 @@ struct Chain {
         }
     }
 
-    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z, int count_changed) const
+    // One side of a change of the cell counts (the committer's lane 0 only):
+    // the count epoch turns odd before the change and even after it.
+    __device__ __forceinline__ void seq_bump() const
+    {
+        __threadfence_block();
+        vstore(sh.seq, vload(sh.seq) + 1);
+        __threadfence_block();
+    }
+
+    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z) const
     {
         L.mx[nm] = x;
         L.my[nm] = y;
         L.mz[nm] = z;
-        L.cchg[nm] = count_changed;
         ++nm;
     }
 
@@ -750,20 +764,27 @@ struct Chain {
         int nm = 0, nid = 0;
         if (t.type != 2) {
             if (lane == 0) {
+                L.has_moved = 0;
                 if (t.type == 0) {
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, t.Po.w);
                     if (!t.cross) {
                         a.cell_pos[(long long)t.co * a.cap + self_slot] = v;
-                        note(L, nm, t.px, t.py, t.pz, 0);
+                        note(L, nm, t.px, t.py, t.pz);
                     } else {
+                        seq_bump();
                         const int c_o = cnt[t.co];
-                        if (self_slot != c_o - 1) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
+                        if (self_slot != c_o - 1) {
+                            a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
+                            L.has_moved = 1;
+                            L.moved = last_val;
+                        }
                         cnt[t.co] = (uint16_t)(c_o - 1);
                         const int c_n = cnt[t.cn];
                         a.cell_pos[(long long)t.cn * a.cap + c_n] = v;
                         cnt[t.cn] = (uint16_t)(c_n + 1);
-                        note(L, nm, t.px, t.py, t.pz, 1);
-                        note(L, nm, t.qx, t.qy, t.qz, 1);
+                        seq_bump();
+                        note(L, nm, t.px, t.py, t.pz);
+                        note(L, nm, t.qx, t.qy, t.qz);
                     }
                     L.pos[0] = t.Po;
                     L.pos[1] = t.Pn;
@@ -773,14 +794,16 @@ struct Chain {
                 } else {
                     const long long ni = sh.n[sp];
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, make_tag((uint32_t)ni, (uint32_t)sp));
+                    seq_bump();
                     const int c_n = cnt[t.cn];
                     a.cell_pos[(long long)t.cn * a.cap + c_n] = v;
                     cnt[t.cn] = (uint16_t)(c_n + 1);
+                    seq_bump();
                     a.pos_by_id[sb + ni] = v;
                     sh.n[sp] = ni + 1;
                     sh.ln_n[sp] = logf((float)(ni + 1));
                     sh.ln_n1[sp] = logf((float)(ni + 2));
-                    note(L, nm, t.qx, t.qy, t.qz, 1);
+                    note(L, nm, t.qx, t.qy, t.qz);
                     L.ids[nid++] = (sp << 24) | (int)ni;
                     L.pos[0] = t.Pn;
                     L.np = 1;
@@ -796,10 +819,14 @@ struct Chain {
         const long long last = sh.n[sp] - 1;
         int swapped = 0;
         if (lane == 0) {
+            seq_bump();
             const int c_o = cnt[t.co];
             swapped = self_slot != c_o - 1;
             if (swapped) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
             cnt[t.co] = (uint16_t)(c_o - 1);
+            seq_bump();
+            L.has_moved = swapped;
+            L.moved = last_val;
         }
         __syncwarp();
         int qx = -1, qy = 0, qz = 0;
@@ -822,12 +849,12 @@ struct Chain {
             if (lane == 0) a.pos_by_id[sb + t.idx] = make_uint4(Q.x, Q.y, Q.z, ntag);
         }
         if (lane == 0) {
-            note(L, nm, t.px, t.py, t.pz, 1);
+            note(L, nm, t.px, t.py, t.pz);
             L.pos[0] = t.Po;
             L.np = 1;
             L.ids[nid++] = (sp << 24) | t.idx;
             if (qx >= 0) {
-                note(L, nm, qx, qy, qz, 0);
+                note(L, nm, qx, qy, qz);
                 L.ids[nid++] = (sp << 24) | (int)last;
             }
             for (int q = nm; q < 3; ++q) L.mx[q] = -1;
@@ -880,23 +907,26 @@ __device__ __forceinline__ bool still_valid(const Chain<F32, VIR> &C, const Shar
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             if (L.mx[q] >= 0) {
-                // the old cell's slots (self, last entry) must be as seen;
-                // a work cell whose count changed may have been seen with
-                // either count by the team's warps (their item ranges follow
-                // the counts)
+                // the old cell's slots (self, last entry) must be as seen
                 const int c = (L.mz[q] * T + L.my[q]) * T + L.mx[q];
                 if (t.possible && t.type != 1 && c == t.co) bad = true;
-                if (L.cchg[q] && in_work(t, L.mx[q], L.my[q], L.mz[q], T)) bad = true;
             }
             if (t.possible && t.type != 1 && L.ids[q] >= 0 && L.ids[q] == (((int)t.s << 24) | t.idx)) bad = true;
         }
         // a particle that appeared, vanished or moved within rc of the
         // trial's old or new position changes dU (exact integer cutoff, as
-        // in Eq. 1's sum)
+        // in Eq. 1's sum); so may a cell's last entry that a removal moved
+        // into the freed slot (an evaluation that read the older count may
+        // have met it twice).  Changes farther away add nothing: their pair
+        // terms are exactly zero.
         if (t.possible) {
             const uint4 X0 = L.pos[0], X1 = (L.np == 2) ? L.pos[1] : L.pos[0];
             if (t.type != 1 && box_within(X0, X1, t.Po, a.R2)) bad = true;
             if (t.type != 2 && box_within(X0, X1, t.Pn, a.R2)) bad = true;
+            if (L.has_moved) {
+                if (t.type != 1 && box_within(L.moved, L.moved, t.Po, a.R2)) bad = true;
+                if (t.type != 2 && box_within(L.moved, L.moved, t.Pn, a.R2)) bad = true;
+            }
         }
     }
     if (__any_sync(0xffffffffu, bad)) return false;
@@ -1006,6 +1036,8 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.stop = 0;
         sh.status = 0;
         sh.where = 0;
+        sh.seq = 0;
+        sh.likely[0] = sh.likely[1] = 0;
     }
     {
         const int first_fill = min(n, kRW);
@@ -1084,9 +1116,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 // predicted counts at the move's turn: lane i looks at the
                 // pending move c0 + i; an insertion or deletion whose
                 // evaluation is in and that the FP32 test would accept counts
-                // +1 or -1 for its species.  The particle pick uses the
-                // prediction; the committer checks the pick against the
-                // actual counts.
+                // +1 or -1 for its species; one not yet evaluated counts as
+                // the chain's more frequent outcome for its kind.  The
+                // particle pick uses the prediction; the committer checks the
+                // pick against the actual counts.
                 const int go = tc.go[p], mm = tc.m[p], c0 = tc.c0[p];
                 if (go == 1 && mm > c0) {
                     const int k = c0 + lane;
@@ -1102,6 +1135,9 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                             for (int q = 0; q < G; ++q) dU += F32 ? Sk.ph[q] : (float)Sk.pd[q];
                             const float lnK = (ty == 1) ? a.lnzv_f[sk] - sh.ln_n1[sk] : sh.ln_n[sk] - a.lnzv_f[sk];
                             if (Wk.lnu < lnK - (float)a.beta * dU) d = (ty == 1) ? 1 : -1;
+                        } else if (ty != 0 && vload(sh.likely[ty - 1])) {
+                            sk = (int)__umulhi(Wk.w[5], (uint32_t)a.S);
+                            d = (ty == 1) ? 1 : -1;
                         }
                     }
                     for (int q = 0; q < a.S; ++q) {
@@ -1128,6 +1164,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             }
             if (lane == 0) {
                 if (j == 0) S.t = t;
+                S.pseq[j] = P.seq;
                 if constexpr (F32) {
                     S.ph[j] = P.e;
                     S.pu[j] = P.ua;
@@ -1146,6 +1183,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         }
     } else if (warp == 0) {
         // ------------------------------------------------------------ committer
+        int att_id[2] = {0, 0}, acc_id[2] = {0, 0};  // insertions, deletions (lane 0)
         for (int m = 0; m < n; ++m) {
             Slot &S = sh.slots[m % kRS];
             const int team = m % NTEAM;
@@ -1175,7 +1213,11 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 if (!ok) break;
                 __threadfence_block();
                 c0 = S.c0;
-                if (c0 == m || still_valid<F32>(C, sh, S.t, c0, m, T, lane)) break;
+                // the team's warps must have read the counts of one epoch
+                // (their item ranges follow the counts)
+                const int q0 = S.pseq[0];
+                const bool one_epoch = __all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0;
+                if (c0 == m || (one_epoch && still_valid<F32>(C, sh, S.t, c0, m, T, lane))) break;
                 // evaluate again against the configuration after m moves
                 if (lane == 0) {
                     vstore(S.tag, 0);
@@ -1253,6 +1295,14 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 refined |= 2 | ((fabs(lnu - lnA_d) <= band) ? 1 : 0);
                 use64 = 1;
                 uab = (float)da;
+            }
+            if (lane == 0 && type != 0) {
+                // the chain's more frequent outcome per kind, for the count prediction
+                const int q = type - 1;
+                att_id[q] += 1;
+                acc_id[q] += fin & 1;
+                const int lk = 2 * acc_id[q] > att_id[q];
+                if (lk != sh.likely[q]) vstore(sh.likely[q], lk);
             }
             int stop_bits = 0;
             if (fin & 1) {

@@ -335,10 +335,20 @@ def test_chain_parity_full_size_c2(precision):
     assert sg["n"] == list(so.n[:1])
 
 
-def test_chain_resume_is_bit_exact():
+def _same_moves(t1, t2, tol):
+    """The same moves and decisions; dU within tol * uabs (the speculative
+    evaluation may split a trial's pair terms among warps differently from
+    one run to the next, so the last bits of dU may differ)."""
+    for k in ("type", "species", "index", "accepted"):
+        assert np.array_equal(t1[k], t2[k]), k
+    ok = np.isfinite(t1["lnA"])
+    assert np.all(np.abs(t1["dU"] - t2["dU"])[ok] <= tol * t1["uabs"][ok] + 1e-300)
+
+
+def test_chain_resume_is_exact():
     """Counter-based moves: [0, a) + [a, b) == [0, b); state export/import
-    resumes.  Bit-exact for a fixed team shape (the shape sets the summation
-    order of the pair terms; decisions never depend on it)."""
+    resumes: identical moves, decisions and configurations (dU and the
+    running energy agree to rounding)."""
     L, pos = _relaxed_workload(800, 0.5, 12)
     types = np.zeros(800, np.int32)
     mix = Mix(1 / 3, 1 / 3, 1 / 3, 0.3, 0.8, [-2.6])
@@ -352,14 +362,17 @@ def test_chain_resume_is_bit_exact():
     _, tb1 = b.run_moves(3, 0, 2500, mix, trace=True)
     snap = b.get_state()
     _, tb2 = b.run_moves(3, 2500, 3500, mix, trace=True)
-    assert np.array_equal(ta, np.concatenate([tb1, tb2]))
+    _same_moves(ta, np.concatenate([tb1, tb2]), TOL["fp64"])
     c = Box(L, 2.5, [[1.0]], [[1.0]])
     c.set_chain_config(1)
     c.restore(*snap)
     _, tc = c.run_moves(3, 2500, 3500, mix, trace=True)
-    assert np.array_equal(tc, tb2)
-    for x, y in zip(a.get_state(), c.get_state()):
+    _same_moves(tc, tb2, TOL["fp64"])
+    sa, sc = a.get_state(), c.get_state()
+    for x, y in zip(sa[:4], sc[:4]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
+    drift = TOL["fp64"] * ta["uabs"][ta["accepted"] == 1].sum() + 1e-9
+    assert abs(sa[4] - sc[4]) <= 2 * drift
 
 
 def test_chain_energy_bookkeeping():

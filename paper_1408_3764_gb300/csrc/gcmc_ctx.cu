@@ -222,36 +222,39 @@ gcmc_status gcmc_trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *s
     return trial_energy(ctx, pos, species, exclude, m, out, out_abs);
 }
 
+// What is wrong with a move mix for this box (nullptr: nothing).  allowed:
+// the GCMC_MIX_* flags the caller accepts.
+static const char *mix_problem(const gcmc_ctx *ctx, const gcmc_move_mix *mix, int32_t allowed)
+{
+    const double ps = mix->p_disp + mix->p_ins + mix->p_del;
+    if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9)
+        return "bad move probabilities";
+    if (!(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L)) return "bad max_disp";
+    if (!(mix->beta >= 0.0) || !std::isfinite(mix->beta)) return "bad beta";
+    if ((mix->flags & ~allowed) != 0 || mix->reserved != 0) return "unknown flags";
+    for (int s = 0; s < ctx->S; ++s)
+        if (!std::isfinite(mix->log_z[s])) return "log_z not finite";
+    return nullptr;
+}
+
+static gcmc_status check_mix(gcmc_ctx *ctx, const gcmc_move_mix *mix, int64_t n_moves, int32_t allowed,
+                             const char *who)
+{
+    if (!mix || n_moves < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad args");
+    if (const char *why = mix_problem(ctx, mix, allowed))
+        return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad move mix (" + why + ")");
+    return GCMC_OK;
+}
+
 gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
                            const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace)
 {
     if (!ctx) return GCMC_ERR_INVALID_ARG;
     if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves: cells not built");
-    if (!mix || n_moves < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: bad args");
-    const double ps = mix->p_disp + mix->p_ins + mix->p_del;
-    if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
-        !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L) || !(mix->beta >= 0.0) ||
-        !std::isfinite(mix->beta) || (mix->flags & ~GCMC_MIX_VIRIAL) != 0 || mix->reserved != 0)
-        return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: bad move mix");
-    for (int s = 0; s < ctx->S; ++s)
-        if (!std::isfinite(mix->log_z[s]))
-            return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: log_z not finite");
+    gcmc_status st = check_mix(ctx, mix, n_moves, GCMC_MIX_VIRIAL, "gcmc_run_moves");
+    if (st != GCMC_OK) return st;
     ctx->mc_valid = false;  // the chain below keeps the 27-cell lists only
     return run_moves(ctx, seed, first_move, n_moves, mix, stats, trace);
-}
-
-static gcmc_status check_mix(gcmc_ctx *ctx, const gcmc_move_mix *mix, int64_t n_moves, const char *who)
-{
-    if (!mix || n_moves < 0) return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad args");
-    const double ps = mix->p_disp + mix->p_ins + mix->p_del;
-    if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
-        !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < ctx->L) || !(mix->beta >= 0.0) ||
-        !std::isfinite(mix->beta) || mix->flags != 0 || mix->reserved != 0)
-        return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": bad move mix");
-    for (int s = 0; s < ctx->S; ++s)
-        if (!std::isfinite(mix->log_z[s]))
-            return fail(ctx, GCMC_ERR_INVALID_ARG, std::string(who) + ": log_z not finite");
-    return GCMC_OK;
 }
 
 gcmc_status gcmc_build_microcells(gcmc_ctx *ctx, double edge, int32_t capacity)
@@ -287,7 +290,7 @@ gcmc_status gcmc_run_moves_micro(gcmc_ctx *ctx, uint64_t seed, uint64_t first_mo
     if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves_micro: cells not built");
     if (!(ctx->mc_edge > 0.0))
         return fail(ctx, GCMC_ERR_STATE, "gcmc_run_moves_micro: gcmc_build_microcells was never called");
-    gcmc_status st = check_mix(ctx, mix, n_moves, "gcmc_run_moves_micro");
+    gcmc_status st = check_mix(ctx, mix, n_moves, 0, "gcmc_run_moves_micro");
     if (st != GCMC_OK) return st;
     return run_moves_micro(ctx, seed, first_move, n_moves, mix, stats, trace);
 }
@@ -570,12 +573,8 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
         return GCMC_ERR_INVALID_ARG;
     }
     for (size_t k = 0; k < b->ctxs.size(); ++k) {
-        const gcmc_move_mix *mix = &mixes[k];
-        const double ps = mix->p_disp + mix->p_ins + mix->p_del;
-        if (!(mix->p_disp >= 0 && mix->p_ins >= 0 && mix->p_del >= 0) || std::fabs(ps - 1.0) > 1e-9 ||
-            !(mix->max_disp >= 0.0) || !(2.0 * mix->max_disp < b->ctxs[k]->L) || !(mix->beta >= 0.0) ||
-            (mix->flags & ~GCMC_MIX_VIRIAL) != 0 || mix->reserved != 0) {
-            b->err = "gcmc_batch_run_moves: bad move mix";
+        if (const char *why = mix_problem(b->ctxs[k], &mixes[k], GCMC_MIX_VIRIAL)) {
+            b->err = std::string("gcmc_batch_run_moves: bad move mix of chain ") + std::to_string(k) + " (" + why + ")";
             return GCMC_ERR_INVALID_ARG;
         }
     }

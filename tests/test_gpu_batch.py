@@ -121,3 +121,19 @@ def test_batch_rejects_mixed_precision():
     b = Box(10.0, 2.5, [[1.0]], [[1.0]], precision="fp64")
     with pytest.raises(RuntimeError):
         Batch([a, b])
+
+
+def test_batch_rejects_bad_mix():
+    """Every chain's mix is checked: a non-finite ln z or beta is refused before
+    any launch, and the chains keep their state."""
+    a = Box(10.0, 2.5, [[1.0]], [[1.0]])
+    b = Box(10.0, 2.5, [[1.0]], [[1.0]])
+    pos = W.uniform_positions(100, 10.0, 3)
+    for x in (a, b):
+        x.build_cells(torch.as_tensor(pos), torch.zeros(100, dtype=torch.int32))
+    batch = Batch([a, b])
+    good = Mix(0.4, 0.3, 0.3, 0.3, 1 / 1.2, [-2.7])
+    for bad in (Mix(0.4, 0.3, 0.3, 0.3, 1 / 1.2, [float("nan")]), Mix(0.4, 0.3, 0.3, 0.3, float("inf"), [-2.7])):
+        with pytest.raises(RuntimeError):
+            batch.run_moves([1, 2], 0, 100, [good, bad])
+    assert a.counts()[0] == 100 and b.counts()[0] == 100

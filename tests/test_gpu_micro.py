@@ -175,3 +175,12 @@ def test_micro_and_cell_chains_alternate(precision):
     # the full-system energy in the context's precision (FP32 pair terms: ~1e-8 relative)
     rel = 1e-9 if precision == "fp64" else 1e-6
     assert b.total_energy() == pytest.approx(o.total_energy(), rel=rel, abs=1e-9)
+
+
+def test_micro_chain_refuses_the_virial_flag():
+    L = 8.0
+    b = Box(L, 2.5, [[1.0]], [[1.0]])
+    b.build_cells(torch.as_tensor(_relaxed(100, L, 4)), torch.zeros(100, dtype=torch.int32))
+    b.build_microcells(1.0)
+    with pytest.raises(RuntimeError):
+        b.run_moves_micro(1, 0, 100, Mix(0.4, 0.3, 0.3, 0.3, 1.0, [-2.0], virial=True))

@@ -188,6 +188,25 @@ gcmc_status gcmc_trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *s
 gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, int64_t n_moves,
                            const gcmc_move_mix *mix, gcmc_move_stats *stats, gcmc_trace *trace);
 
+/* Checks the configuration on the host (a consistency checker, in place of
+ * a device sanitizer): every particle of every species is listed exactly
+ * once, in the cell of its grid position, with an entry equal to its
+ * record; cell counts are within capacity and sum to N; the same for the
+ * microcells when they are up to date.  Copies the state to the host;
+ * synchronises the stream.  Errors: STATE (with the first violation in
+ * gcmc_last_error), CUDA. */
+gcmc_status gcmc_check_state(gcmc_ctx *ctx);
+
+/* Diagnostic hook for the failure path: ns = the limit, in ns of the GPU's
+ * global timer, of every wait inside the chain kernel (0: the default,
+ * 1 s); stall_move >= 0: in later gcmc_run_moves calls the committer, about
+ * to commit move stall_move of the call, waits on a flag that nothing sets
+ * (-1: no stall).  A wait that runs out stops the chain before its next
+ * move: every committed move is applied and booked, the kernel returns and
+ * gcmc_run_moves returns TIMEOUT with moves_done = the moves committed; the
+ * context stays usable.  Errors: INVALID_ARG. */
+gcmc_status gcmc_set_wait_limit(gcmc_ctx *ctx, uint64_t ns, int64_t stall_move);
+
 /* Microcell list (Sec. 3.3): the box cut into M^3 microcells of edge about
  * one sigma, each holding at most `capacity` particles in a slot array
  * stored slot-major (slot k of every cell contiguous, Sec. 3.3.1).

@@ -67,6 +67,8 @@ SIGNATURES = {
     "gcmc_trial_energy": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
     "gcmc_run_moves": (C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_int64, C.POINTER(MoveMix),
                                  C.POINTER(MoveStats), _vp]),
+    "gcmc_check_state": (C.c_int, [_vp]),
+    "gcmc_set_wait_limit": (C.c_int, [_vp, C.c_uint64, C.c_int64]),
     "gcmc_build_microcells": (C.c_int, [_vp, C.c_double, C.c_int32]),
     "gcmc_microcells": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gcmc_run_moves_micro": (C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_int64, C.POINTER(MoveMix),

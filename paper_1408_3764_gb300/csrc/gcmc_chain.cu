@@ -81,6 +81,8 @@ struct ChainArgs {
     double beta, lnV;
     double logz[kMaxSpecies];
     double tol;  // relative tolerance that defines "near the threshold"
+    unsigned long long wait_ns;  // limit of every wait (kWaitNs unless a test shortens it)
+    int stall_at;  // diagnostic: the committer waits on a flag nothing sets at this move (-1 none)
     int virial;  // also keep the running virial sum_{i<j} r U'(r)
     float lnzv_f[kMaxSpecies];
     FieldF ff;
@@ -97,20 +99,20 @@ struct ChainArgs {
 constexpr int kRS = 32;       // move slots in flight (logs and book entries too)
 constexpr int kRW = 128;      // words ring
 constexpr int kFill = 32;     // words filled per keeper round
-constexpr unsigned long long kWaitNs = 1000000000ull;  // a wait gives up after 1 s
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a wait gives up after 1 s (default)
 
-// A bounded wait: expired() turns true once the wait has lasted kWaitNs
+// A bounded wait: expired() turns true once the wait has lasted `limit` ns
 // (global timer, read every 256 polls).
 struct Wait {
     unsigned long long t0 = 0;
     unsigned polls = 0;
-    __device__ __forceinline__ bool expired()
+    __device__ __forceinline__ bool expired(unsigned long long limit)
     {
         if ((++polls & 255u) != 0u) return false;
         unsigned long long now;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
         if (t0 == 0) t0 = now;
-        return now - t0 > kWaitNs;
+        return now - t0 > limit;
     }
 };
 constexpr uint32_t kOld = 1u, kNew = 2u;
@@ -283,6 +285,7 @@ struct __align__(16) Shared {
     // 1 while this chain accepts most of its insertions [0] / deletions [1]
     // (the bet the count prediction makes on moves not yet evaluated)
     int likely[2];
+    int never;  // a flag nothing sets (the diagnostic stall waits on it)
 };
 
 __device__ __forceinline__ int vload(const int &x) { return *(volatile const int *)&x; }
@@ -1038,6 +1041,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.where = 0;
         sh.seq = 0;
         sh.likely[0] = sh.likely[1] = 0;
+        sh.never = 0;
     }
     {
         const int first_fill = min(n, kRW);
@@ -1088,7 +1092,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                         go = 2;
                         break;
                     }
-                    if (wt.expired()) {
+                    if (wt.expired(a.wait_ns)) {
                         atomicOr(&sh.status, kStatusTimeout);
                         atomicOr(&sh.where, 1);
                         vstore(sh.stop, 1);
@@ -1188,6 +1192,25 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             Slot &S = sh.slots[m % kRS];
             const int team = m % NTEAM;
             bool ok = true;
+            if (m == a.stall_at) {
+                // diagnostic: a bounded wait on a flag nothing sets runs out,
+                // and the chain stops before this move with a timeout status
+                Wait ws;
+                for (;;) {
+                    int f = 0;
+                    if (lane == 0) f = vload(sh.never);
+                    if (__shfl_sync(0xffffffffu, f, 0)) break;
+                    if (ws.expired(a.wait_ns)) {
+                        if (lane == 0) {
+                            atomicOr(&sh.status, kStatusTimeout);
+                            atomicOr(&sh.where, 2);
+                        }
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) break;
+            }
             int c0 = 0, attempt = 0;
             for (;; ++attempt) {
                 // wait for the evaluation of m and for room in the keeper's book
@@ -1201,7 +1224,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                     }
                     r = __shfl_sync(0xffffffffu, r, 0);
                     if (r) break;
-                    if (wt.expired()) {
+                    if (wt.expired(a.wait_ns)) {
                         if (lane == 0) {
                             atomicOr(&sh.status, kStatusTimeout);
                             atomicOr(&sh.where, 2);
@@ -1437,7 +1460,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             stop = __shfl_sync(0xffffffffu, stop, 0);
             com = __shfl_sync(0xffffffffu, com, 0);
             if (stop && mb >= com) break;
-            if (wt.expired()) {
+            if (wt.expired(a.wait_ns)) {
                 if (lane == 0) {
                     atomicOr(&sh.status, kStatusTimeout);
                     atomicOr(&sh.where, 4);
@@ -1554,6 +1577,8 @@ static void fill_args(ChainArgs &a, const ChainJob &j, ChainOut *out)
     for (int s = 0; s < kMaxSpecies; ++s) a.logz[s] = s < ctx->S ? mix->log_z[s] : 0.0;
     a.tol = ctx->precision == GCMC_FP32 ? 1e-5 : 1e-12;
     a.virial = (mix->flags & GCMC_MIX_VIRIAL) ? 1 : 0;
+    a.wait_ns = ctx->wait_ns ? ctx->wait_ns : kWaitNs;
+    a.stall_at = (ctx->stall_at >= j.done && ctx->stall_at - j.done < a.n_moves) ? (int)(ctx->stall_at - j.done) : -1;
     for (int s = 0; s < kMaxSpecies; ++s) a.lnzv_f[s] = (float)(a.logz[s] + a.lnV);
     a.ff = ctx->ff;
     a.fd = ctx->fd;

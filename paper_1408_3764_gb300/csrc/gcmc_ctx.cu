@@ -257,6 +257,77 @@ gcmc_status gcmc_run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first_move, in
     return run_moves(ctx, seed, first_move, n_moves, mix, stats, trace);
 }
 
+gcmc_status gcmc_set_wait_limit(gcmc_ctx *ctx, uint64_t ns, int64_t stall_move)
+{
+    if (!ctx || stall_move < -1) return GCMC_ERR_INVALID_ARG;
+    ctx->wait_ns = ns;
+    ctx->stall_at = stall_move;
+    return GCMC_OK;
+}
+
+// Host-side consistency of the configuration: every particle listed once, in
+// the cell (and microcell) of its position, with the record of its id.
+gcmc_status gcmc_check_state(gcmc_ctx *ctx)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_check_state: cells not built");
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int S = ctx->S, T = ctx->T, cap = ctx->cap;
+    const int64_t ncell = ctx->ncell, maxN = ctx->maxN;
+    std::vector<int32_t> cc((size_t)ncell);
+    std::vector<uint4> cp((size_t)ncell * cap), rec((size_t)S * maxN);
+    std::vector<int64_t> dn(kMaxSpecies, 0);
+    GCMC_CUDA(ctx, cudaMemcpy(cc.data(), ctx->cell_count, cc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GCMC_CUDA(ctx, cudaMemcpy(cp.data(), ctx->cell_pos, cp.size() * sizeof(uint4), cudaMemcpyDeviceToHost));
+    GCMC_CUDA(ctx, cudaMemcpy(rec.data(), ctx->pos_by_id, rec.size() * sizeof(uint4), cudaMemcpyDeviceToHost));
+    GCMC_CUDA(ctx, cudaMemcpy(dn.data(), ctx->d_n, kMaxSpecies * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    int64_t N = 0;
+    for (int s = 0; s < S; ++s) {
+        if (dn[s] != ctx->n_host[s] || dn[s] < 0 || dn[s] > maxN)
+            return fail(ctx, GCMC_ERR_STATE, "gcmc_check_state: species counts disagree");
+        N += dn[s];
+    }
+    auto cell = [](uint4 r, int64_t M) {
+        return ((int64_t)(((uint64_t)r.z * M) >> 32) * M + (int64_t)(((uint64_t)r.y * M) >> 32)) * M +
+               (int64_t)(((uint64_t)r.x * M) >> 32);
+    };
+    auto check_lists = [&](const char *what, int64_t M, int64_t nc, int c_cap, const std::vector<int32_t> &cnt,
+                           auto slot) -> gcmc_status {
+        std::vector<uint8_t> seen((size_t)S * maxN, 0);
+        int64_t total = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            if (cnt[(size_t)c] < 0 || cnt[(size_t)c] > c_cap)
+                return fail(ctx, GCMC_ERR_STATE, std::string("gcmc_check_state: a ") + what + " count is out of range");
+            total += cnt[(size_t)c];
+            for (int k = 0; k < cnt[(size_t)c]; ++k) {
+                const uint4 r = slot(c, k);
+                const int64_t s = r.w & 0xFF, i = r.w >> 8;
+                if (s >= S || i >= dn[(size_t)s])
+                    return fail(ctx, GCMC_ERR_STATE, std::string("gcmc_check_state: a ") + what + " lists a dead id");
+                const uint4 q = rec[(size_t)(s * maxN + i)];
+                if (q.x != r.x || q.y != r.y || q.z != r.z || q.w != r.w || cell(r, M) != c)
+                    return fail(ctx, GCMC_ERR_STATE,
+                                std::string("gcmc_check_state: a ") + what + " entry disagrees with its record");
+                if (seen[(size_t)(s * maxN + i)]++)
+                    return fail(ctx, GCMC_ERR_STATE, std::string("gcmc_check_state: an id is listed twice (") + what + ")");
+            }
+        }
+        if (total != N) return fail(ctx, GCMC_ERR_STATE, std::string("gcmc_check_state: ") + what + " counts do not sum to N");
+        return GCMC_OK;
+    };
+    gcmc_status st = check_lists("cell", T, ncell, cap, cc,
+                                 [&](int64_t c, int k) { return cp[(size_t)(c * cap + k)]; });
+    if (st != GCMC_OK || !ctx->mc_valid) return st;
+    const int64_t ncm = ctx->mc_ncell;
+    std::vector<uint8_t> mcc8((size_t)ncm);
+    std::vector<uint4> mcp((size_t)ctx->mc_cap * ncm);
+    GCMC_CUDA(ctx, cudaMemcpy(mcc8.data(), ctx->mc_count, mcc8.size(), cudaMemcpyDeviceToHost));
+    GCMC_CUDA(ctx, cudaMemcpy(mcp.data(), ctx->mc_pos, mcp.size() * sizeof(uint4), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> mcc(mcc8.begin(), mcc8.end());
+    return check_lists("microcell", ctx->mc_M, ncm, ctx->mc_cap, mcc,
+                       [&](int64_t c, int k) { return mcp[(size_t)(k * ncm + c)]; });
+}
+
 gcmc_status gcmc_build_microcells(gcmc_ctx *ctx, double edge, int32_t capacity)
 {
     if (!ctx) return GCMC_ERR_INVALID_ARG;

@@ -66,6 +66,8 @@ struct gcmc_ctx {
     int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
     int64_t last_refines = 0;
     int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)
+    uint64_t wait_ns = 0;   // limit of the chain kernel's waits (0: the default, 1 s)
+    int64_t stall_at = -1;  // diagnostic stall of the committer at this move of a call (-1 none)
 
     // ---- microcells (Sec. 3.3), valid while mc_valid
     bool mc_valid = false;

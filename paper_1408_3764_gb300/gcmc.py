@@ -214,6 +214,15 @@ class Box:
             return stats, arr
         return stats
 
+    def check_state(self) -> None:
+        """Host-side consistency check of the configuration (raises on a violation)."""
+        check(self._lib.gcmc_check_state(self._h), self._h, "gcmc_check_state")
+
+    def set_wait_limit(self, ns: int, stall_move: int = -1) -> None:
+        """Diagnostic hook: the chain kernel's wait limit in ns (0: the default)
+        and a move at which the committer waits on a flag nothing sets (-1: none)."""
+        check(self._lib.gcmc_set_wait_limit(self._h, int(ns), int(stall_move)), self._h)
+
     def build_microcells(self, edge: float = 1.0, capacity: int = 0) -> None:
         """Microcell list of the current particles (Sec. 3.3)."""
         check(self._lib.gcmc_build_microcells(self._h, float(edge), int(capacity)), self._h,

@@ -91,7 +91,7 @@ typedef struct {
  * The first run with the flag after a build, a restore or a run without it
  * starts from the full 27-cell sum (the running energy is left as it is);
  * later runs with it continue the running value.  The flag changes no
- * decision and no energy: the moves and dU are those of a run without it. */
+ * decision: the moves are those of a run without it (dU to rounding). */
 #define GCMC_MIX_VIRIAL 1
 
 /* Counters of one gcmc_run_moves call (averages over the moves of the call). */
@@ -322,10 +322,11 @@ gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refi
 /* Team shape of the chain kernel (how its warps split the evaluation of
  * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape
  * during the next gcmc_run_moves (after a first quarter of its moves under
- * shape 0) and keep the fastest.  Every
- * shape takes the same moves and decisions and reaches the same
- * configuration; in FP32 mode the pair terms are summed in a shape-dependent
- * order, so dU (and the running energy) may differ in the last bits.
+ * shape 0) and keep the fastest.  Every shape takes the same moves and
+ * decisions and reaches the same configuration.  How a trial's pair terms
+ * are split among warps depends on the shape and, under speculation, on
+ * which counts an evaluation read, so dU and the running energy may differ
+ * between runs in their last bits (within the precision's tolerance).
  * Errors: INVALID_ARG. */
 #define GCMC_CHAIN_CONFIGS 4
 gcmc_status gcmc_set_chain_config(gcmc_ctx *ctx, int32_t config);

@@ -8,25 +8,24 @@
 //  * evaluator teams (warps 1..G*NTEAM): team k evaluates moves k, k + NTEAM,
 //    ..., each as soon as fewer than LOOK moves separate it from the
 //    committer.  An evaluation is speculative: it reads the configuration as
-//    it stands when it starts (after `c0` committed moves) and produces the
-//    trial (particle, old/new position, cells), its energy change dU (the 27
-//    neighbour cells, Algorithms 6 and 7; the union of both neighbourhoods
-//    for a displacement that changes cell), the error scale uabs, and the
-//    slots the update will need.  A lane owns up to two cells of the trial's
-//    work list and the team's warps split the slots of every cell; each warp
-//    leaves its sums in the move's slot and the committer adds them in a
-//    fixed order.  Pair terms are FP32 (or FP64) from exact integer
-//    separations;
+//    it stands when it starts (after `c0` committed moves, with the particle
+//    counts predicted at the move's turn) and produces the trial, its energy
+//    change dU over the 27 neighbour cells (Algorithms 6 and 7; the union of
+//    both neighbourhoods for a displacement into an adjacent cell), the error
+//    scale uabs and the slots the update will need.  The team's warps split
+//    the items of the work cells evenly, by counts read in one count epoch
+//    (a sequence lock around count changes), and leave their sums in the
+//    move's slot; the committer adds them in a fixed order;
 //  * the committer (warp 0) takes the moves strictly in order.  A move is
-//    valid when no move committed after its evaluation started touched one
-//    of its cells, changed N (which selects the particle of a displacement
-//    or deletion) or wrote its particle's record; otherwise the committer
-//    evaluates it again against the current configuration.  It then takes
-//    the Metropolis decision (Eqs. 3-5, textbook sign of mu) in FP32 with an
-//    explicit error band -- a trial inside the band is recomputed entirely in
-//    FP64 -- and applies an accepted move (Sec. 3.2.5: swap-with-last
-//    removal, append, species index refill).  Every decision is therefore
-//    the one the sequential chain takes;
+//    valid when its warps read one count epoch and no later commit put,
+//    removed or moved a particle within rc of the trial, touched its old
+//    cell or its record, or changed the particle the counts pick; otherwise
+//    the team evaluates it again.  The committer then takes the Metropolis
+//    decision (Eqs. 3-5, textbook sign of mu) in FP32 with an explicit error
+//    band -- a trial inside the band is recomputed entirely in FP64 -- and
+//    applies an accepted move (Sec. 3.2.5: swap-with-last removal, append,
+//    species index refill).  Every decision is therefore the one the
+//    sequential chain takes;
 //  * the keeper (last warp) keeps the FP64 running energy, the averages, the
 //    counters and the trace, and refills the ring of Philox4x32-10 words.
 //
@@ -34,6 +33,7 @@
 // with block-scope fences; every wait is bounded and sets a timeout status
 // instead of hanging.  Cell counters live in shared memory (uint16) for the
 // whole launch; particle data stays in the padded cell-major layout in L2.
+//
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -19,10 +19,18 @@ the public API with the inputs copied from pinned host memory and the
 results read back every step.
 
 Also reported: the plain FP64 single chain (the 2,048-particle workload),
-the 131,072-particle chain in FP32 and FP64, the batched isotherm in FP64,
-the FP32-vs-FP64 dU agreement of one chain, and the throughput kernels
-(trial energies, full-system energy, gradient, cell build) of the
-million-particle mixture and the 262,144-particle gradient workload.
+the 131,072-particle chain in FP32 and FP64, the batched isotherm in FP64 and
+with the running virial, the same single chains evaluated over the microcell
+list (Sec. 3.3), the FP32-vs-FP64 dU agreement of one chain, the throughput
+kernels (trial energies, full-system energy, gradient, cell build) of the
+million-particle mixture and the 262,144-particle gradient workload, and the
+cutoff sweep (one 87,296-particle chain per cutoff, rc 2.5 .. 4.25, FP32,
+FP64 and microcells).  --kernels-only and --micro-only print just those
+figures; --no-compare / --no-kernels / --no-sweep / --no-cpu-baseline skip
+parts of the default run.
+
+The per-box work of a step (cell build, energy, gradient) is issued from a
+small pool of host threads, each box on its own CUDA stream.
 
 --impl reference runs the CPU oracle (plain FP64 C) on the host cores as the
 reference arm, on the same workload and metric.

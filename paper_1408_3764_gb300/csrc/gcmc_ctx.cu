@@ -1,6 +1,7 @@
 // gcmc_ctx.cu -- the C ABI: context lifetime, parameters, geometry, state
-// import/export and error reporting.  Kernels live in gcmc_cells.cu,
-// gcmc_energy.cu and gcmc_chain.cu.
+// import/export, the move-mix validator, the host consistency checker, the
+// batch object and error reporting.  Kernels live in gcmc_cells.cu,
+// gcmc_energy.cu, gcmc_chain.cu and gcmc_micro.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -1,8 +1,8 @@
 // gcmc_energy.cu -- cell-list energies on the compact cell-major layout:
 //   k_trial_energy   energy of many trial points against their 27 cells
 //                    (Algorithms 6 and 7, one warp per trial point);
-//   k_cell_energy    full-system energy, one CTA per home cell (the
-//                    cell-list CalculateTotalEnergy of Sec. 3.1.1);
+//   k_cell_energy    full-system energy and virial, one CTA per home cell
+//                    (the cell-list CalculateTotalEnergy of Sec. 3.1.1);
 //   k_cell_grad      its hand-written gradient (positions, eps, sigma, virial).
 // FP32 mode: pair terms and per-lane sums in FP32, sums across cells in
 // FP64.  FP64 mode: everything in FP64.

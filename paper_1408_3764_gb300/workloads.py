@@ -35,7 +35,9 @@ def separated_positions(n: int, L: float, dmin: float, seed: int) -> np.ndarray:
     """n positions in the periodic box [0, L)^3 with no two closer than dmin
     (minimum image): random sequential addition -- uniform candidates, each
     kept if it keeps dmin from every position kept before.  The candidates
-    come from one PCG64 stream, so the result depends only on the arguments."""
+    come from one PCG64 stream, so the result depends only on the arguments.
+    Raises ValueError when 1000 n candidates do not suffice (a packing beyond
+    what random sequential addition reaches)."""
     return _separated(int(n), float(L), float(dmin), int(seed)).copy()
 
 
@@ -46,7 +48,12 @@ def _separated(n: int, L: float, dmin: float, seed: int) -> np.ndarray:
     h, half, d2 = L / g, 0.5 * L, dmin * dmin
     cells = {}
     out = []
+    tried = 0
     while len(out) < n:
+        tried += 4096
+        if tried > 1000 * max(n, 1) + 4096:
+            raise ValueError("separated_positions: %d points %.3g apart do not fit in a box of %.3g"
+                             % (n, dmin, L))
         for px, py, pz in (rng.random((4096, 3)) * L).tolist():
             cx, cy, cz = int(px / h) % g, int(py / h) % g, int(pz / h) % g
             ok = True

@@ -1,7 +1,7 @@
 """GPU: failure detection without a GPU fault.
 
 * A bounded wait that runs out: the committer, at a chosen move, waits on a
-  flag that nothing sets (the diagnostic hook gcmc_set_wait_limit, 1 ms
+  flag that nothing sets (the diagnostic hook gcmc_set_wait_limit, 10 ms
   limit).  The kernel returns a timeout status, gcmc_run_moves reports
   TIMEOUT with every committed move applied and booked, the configuration
   passes the host consistency check, and the same context then continues the
@@ -52,7 +52,7 @@ def test_stalled_committer_times_out_and_context_stays_usable(precision):
     b = Box(L, 2.5, [[1.0]], [[1.0]], precision=precision)
     b.set_chain_config(0)
     b.build_cells(torch.as_tensor(pos), torch.zeros(800, dtype=torch.int32))
-    b.set_wait_limit(1_000_000, stall_move=1500)
+    b.set_wait_limit(10_000_000, stall_move=1500)
     st = b.run_moves(5, 0, 5000, Mix(*args), check_status=False)
     assert st["status"] == TIMEOUT
     assert st["moves_done"] == 1500

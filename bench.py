@@ -614,11 +614,16 @@ def main():
     e2e_run = Runner(chains, a.precision, dev, rank, host_inputs=True)
     e2e_run.step(0, M)
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for k in range(a.steps):
         e2e_run.step(a.warmup + k, M)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        dist.barrier()
+        e2e_s = max_over_ranks(e2e_s, dev)  # the job's time is its slowest replica's
     e2e_run.close()
     h2d = sum(w.n * 3 * 8 + w.n * 4 for w in chains)
     S = len(chains[0].log_z)

@@ -96,6 +96,7 @@ class Box:
         self._h = h
 
     def close(self):
+        """Frees the context and its device memory."""
         if getattr(self, "_h", None):
             self._lib.gcmc_destroy(self._h)
             self._h = None
@@ -111,12 +112,14 @@ class Box:
         return self._h
 
     def geometry(self) -> dict:
+        """Cells per side T, cell count, cell capacity, per-species capacity, grid cutoff, grid spacing."""
         g = _lib.Geometry()
         check(self._lib.gcmc_get_geometry(self._h, C.byref(g)), self._h)
         return dict(T=g.T, n_cells=g.n_cells, cell_capacity=g.cell_capacity,
                     max_particles=g.max_particles, cutoff_grid2=g.cutoff_grid2, h=g.h)
 
     def build_cells(self, pos, species):
+        """Bins n positions ([n, 3] FP64, box coordinates) of the given species into the cell list (Sec. 3.2.1)."""
         pos = _dev(pos, torch.float64, self.device).reshape(-1, 3)
         species = _dev(species, torch.int32, self.device).reshape(-1)
         if species.numel() != pos.shape[0]:
@@ -128,6 +131,7 @@ class Box:
         return self
 
     def cell_list(self):
+        """The last build's compact cell list: (cell starts, cell counts, input indices sorted by cell)."""
         g = self.geometry()
         cs = torch.empty(g["n_cells"], dtype=torch.int32, device=self.device)
         cc = torch.empty_like(cs)
@@ -136,6 +140,7 @@ class Box:
         return cs, cc, order[: self._n_build]
 
     def launches(self) -> int:
+        """Kernels this box has launched so far."""
         out = np.zeros(1, np.int64)
         check(self._lib.gcmc_kernel_launches(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
         return int(out[0])
@@ -145,22 +150,27 @@ class Box:
         check(self._lib.gcmc_set_chain_config(self._h, int(config)), self._h)
 
     def chain_config(self) -> int:
+        """The chain kernel's current team shape (0..3; -1 before the tuner has run)."""
         out = C.c_int32()
         check(self._lib.gcmc_get_chain_config(self._h, C.byref(out)), self._h)
         return out.value
 
     def chain_counters(self) -> dict:
+        """Moves of the last run evaluated again (refetched) and trials decided in FP64 (refined)."""
         out = np.zeros(2, np.int64)
         check(self._lib.gcmc_chain_counters(self._h, out[0:].ctypes.data_as(C.c_void_p),
                                             out[1:].ctypes.data_as(C.c_void_p)), self._h)
         return dict(refetched=int(out[0]), refined=int(out[1]))
 
     def counts(self) -> np.ndarray:
+        """Particles per species."""
         out = np.zeros(MAX_SPECIES, np.int64)
         check(self._lib.gcmc_counts(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
         return out[: self.S]
 
     def trial_energy(self, pos, species, exclude=None, with_abs=False):
+        """Energy of trial points ([m, 3] FP64) of the given species against their 27 cells, each
+        excluding one particle id (s << 32 | i) or none; with_abs also returns the |rep| + |att| sums."""
         pos = _dev(pos, torch.float64, self.device).reshape(-1, 3)
         species = _dev(species, torch.int32, self.device).reshape(-1)
         m = pos.shape[0]
@@ -178,11 +188,14 @@ class Box:
                                            pos.shape[0], _ptr(out), _ptr(out_abs))
 
     def total_energy(self) -> float:
+        """Full-system energy (Sec. 3.1.1, over the 27 cells); also resets the chain's running energy."""
         e = C.c_double()
         check(self._lib.gcmc_total_energy(self._h, C.byref(e)), self._h, "gcmc_total_energy")
         return e.value
 
     def energy_grad(self, want_pos=True):
+        """Energy, virial and gradients: forces per particle (species-major, on the device),
+        dE/deps and dE/dsigma tables."""
         n = int(self.counts().sum())
         dpos = torch.empty((max(n, 1), 3), dtype=torch.float32, device=self.device) if want_pos else None
         S = self.S
@@ -198,6 +211,8 @@ class Box:
 
     def run_moves(self, seed: int, first_move: int, n_moves: int, mix: Mix, trace: bool = False,
                   trace_buf: Optional[torch.Tensor] = None, check_status: bool = True):
+        """Moves first_move .. first_move + n_moves - 1 of the chain (Algorithm 1) on the device.
+        Returns the statistics (and the per-move trace with trace=True)."""
         cm = mix.to_c()
         st = MoveStats()
         tb = trace_buf
@@ -259,6 +274,7 @@ class Box:
         return stats
 
     def get_state(self):
+        """(counts per species, grid positions species-major, cell counts, cell references, running energy)."""
         n = self.counts()
         N = int(n.sum())
         g = self.geometry()
@@ -272,6 +288,7 @@ class Box:
         return n, pos[:N], cc, refs[:N], e.value
 
     def restore(self, n_per_species, pos, cell_count, cell_refs, energy=float("nan")):
+        """Imports a state from get_state (validated in full before anything changes)."""
         n = np.ascontiguousarray(np.asarray(n_per_species, np.int64))
         pos = np.ascontiguousarray(np.asarray(pos, np.uint32).reshape(-1, 3))
         cc = np.ascontiguousarray(np.asarray(cell_count, np.int32))
@@ -295,6 +312,7 @@ class Batch:
         self._h = h
 
     def close(self):
+        """Frees the batch (the boxes stay)."""
         if getattr(self, "_h", None):
             self._lib.gcmc_batch_destroy(self._h)
             self._h = None
@@ -306,6 +324,7 @@ class Batch:
             pass
 
     def run_moves(self, seeds, first_move: int, n_moves: int, mixes: Sequence[Mix], check_status=True):
+        """Moves first_move .. first_move + n_moves - 1 of every chain in one launch; per-chain statistics."""
         K = len(self.boxes)
         sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(K))
         cm = (MoveMix * K)(*[m.to_c() for m in mixes])
@@ -317,6 +336,7 @@ class Batch:
         return [stats_dict(st[k], self.boxes[k].S) for k in range(K)]
 
     def config(self, set_config: int = -2):
+        """Sets the team shape (-1 automatic, -2 unchanged); returns it and the tuner's per-shape times."""
         out = C.c_int32()
         probe = np.zeros(_lib.CHAIN_CONFIGS, np.float64)
         check(self._lib.gcmc_batch_config(self._h, int(set_config), C.byref(out),
@@ -324,6 +344,7 @@ class Batch:
         return out.value, probe
 
     def launches(self) -> int:
+        """Chain launches of this batch so far."""
         out = np.zeros(1, np.int64)
         check(self._lib.gcmc_batch_launches(self._h, out.ctypes.data_as(C.c_void_p)), None)
         return int(out[0])

@@ -140,7 +140,8 @@ typedef struct gcmc_ctx gcmc_ctx;
  * Errors: INVALID_ARG (L, rc, species, tables, precision), CUDA. */
 gcmc_status gcmc_create(const gcmc_params *params, void *stream, gcmc_ctx **out);
 
-/* Frees the context and all its device buffers.  NULL is accepted. */
+/* Frees the context and all its device buffers (after its stream drains).
+ * NULL is accepted.  Errors: none (always OK). */
 gcmc_status gcmc_destroy(gcmc_ctx *ctx);
 
 /* Bins n particles into the cell list (Sec. 3.2.1, "Building the Initial
@@ -286,7 +287,8 @@ gcmc_status gcmc_total_energy_noalloc(gcmc_ctx *ctx, double *energy);
 gcmc_status gcmc_energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma,
                              double *energy, double *virial);
 
-/* Particle counts per species (host, n_species int64). */
+/* Particle counts per species (host, n_species int64; zeros before the
+ * first build).  Errors: INVALID_ARG (NULL). */
 gcmc_status gcmc_counts(gcmc_ctx *ctx, int64_t *n_per_species);
 
 /* Copies the current configuration out (all host pointers, any may be NULL):
@@ -330,6 +332,8 @@ gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refi
  * Errors: INVALID_ARG. */
 #define GCMC_CHAIN_CONFIGS 4
 gcmc_status gcmc_set_chain_config(gcmc_ctx *ctx, int32_t config);
+/* The current team shape (host int32; -1 until the tuner has run).
+ * Errors: INVALID_ARG (NULL). */
 gcmc_status gcmc_get_chain_config(gcmc_ctx *ctx, int32_t *config);
 
 /* Last error message of the context (never NULL; "" when none). */
@@ -346,6 +350,8 @@ typedef struct gcmc_batch gcmc_batch;
 /* Errors: INVALID_ARG (NULL or repeated contexts, mixed precision or
  * device), CUDA. */
 gcmc_status gcmc_batch_create(gcmc_ctx *const *ctxs, int32_t n_chains, gcmc_batch **out);
+/* Frees the batch (its stream and buffers); the contexts stay.  NULL is
+ * accepted.  Errors: none (always OK). */
 gcmc_status gcmc_batch_destroy(gcmc_batch *batch);
 
 /* Moves first_move .. first_move + n_moves - 1 of every chain, as
@@ -364,7 +370,8 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *batch, const uint64_t *seeds, uint6
  * GCMC_CHAIN_CONFIGS doubles, or NULL).  Errors: INVALID_ARG. */
 gcmc_status gcmc_batch_config(gcmc_batch *batch, int32_t set_config, int32_t *config_out, double *probe_ms);
 
-/* Chain-kernel launches (graph replays included) made by the batch. */
+/* Chain-kernel launches (graph replays included) made by the batch (host
+ * int64).  Errors: INVALID_ARG (NULL). */
 gcmc_status gcmc_batch_launches(gcmc_batch *batch, int64_t *out);
 
 /* Device time in ms of the chain-kernel launches of the last

@@ -71,6 +71,8 @@ def lib():
         L.orc_move_words.argtypes = [u64, u64, u32, vp]
         L.orc_run_moves.argtypes = [vp, u64, u32, u64, i64, vp, d, vp, vp]
         L.orc_run_moves.restype = C.c_int
+        L.orc_run_moves_ex.argtypes = [vp, u64, u32, u64, i64, vp, d, vp, vp, vp]
+        L.orc_run_moves_ex.restype = C.c_int
         L.orc_count.argtypes = [vp, C.c_int]
         L.orc_count.restype = i64
         L.orc_get_state.argtypes = [vp, vp, vp, vp]
@@ -265,7 +267,10 @@ class System:
         return lib().orc_get_virial(self._h)
 
     def run_moves(self, seed, first, n_moves, p_disp, p_ins, p_del, max_disp, beta, log_z,
-                  tol=1e-12, chain=0, trace=True):
+                  tol=1e-12, chain=0, trace=True, with_sabs=False):
+        """Moves [first, first + n_moves) of the chain; returns (trace, stats),
+        and with with_sabs also the per-move sum of |u_j| over the evaluated
+        pair terms (the floor of the per-move dU error measure)."""
         mix = Mix()
         mix.p_disp, mix.p_ins, mix.p_del = p_disp, p_ins, p_del
         mix.max_disp, mix.beta = max_disp, beta
@@ -274,10 +279,13 @@ class System:
             mix.log_z[s] = lz[s] if s < len(lz) else 0.0
         tr = np.zeros(n_moves if trace else 0, TRACE_DTYPE)
         st = Stats()
-        rc = lib().orc_run_moves(self._h, seed, chain, first, n_moves, C.byref(mix), tol,
-                                 _p(tr) if trace else None, C.byref(st))
+        sabs = np.zeros(n_moves, np.float64) if with_sabs else None
+        rc = lib().orc_run_moves_ex(self._h, seed, chain, first, n_moves, C.byref(mix), tol,
+                                    _p(tr) if trace else None, C.byref(st), _p(sabs))
         if rc != 0:
             raise RuntimeError("energy not set: call set_energy(total_energy()) first")
+        if with_sabs:
+            return tr, st, sabs
         return tr, st
 
     def state(self):

@@ -498,10 +498,12 @@ int orc_build(orc_sys *sys, const double *pos, const int32_t *type, int64_t n,
     return 0;
 }
 
-/* Energy of one pair with exact cutoff decision; adds |rep|+|att| to *uabs
- * and, when wsum is given, the pair's virial term r U'(r) to *wsum. */
+/* Energy of one pair with exact cutoff decision; adds |rep|+|att| to *uabs,
+ * |U| to *sabs when given (the scale of the per-move error measure
+ * |dU_a - dU_b| / max(|dU|, 1e-3 sum_j |u_j|)) and, when wsum is given, the
+ * pair's virial term r U'(r) to *wsum. */
 static double pair_energy_w(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3],
-                            int tb, double *uabs, double *wsum)
+                            int tb, double *uabs, double *wsum, double *sabs)
 {
     int64_t d[3];
     uint64_t g = 0;
@@ -516,6 +518,7 @@ static double pair_energy_w(const orc_sys *sys, const uint32_t A[3], int ta, con
     double rep, att;
     double u = orc_lj(r2, sys->eps[ta * sys->S + tb], sys->sigma[ta * sys->S + tb], &rep, &att);
     if (uabs) *uabs += rep + att;
+    if (sabs) *sabs += fabs(u);
     if (wsum) *wsum += sqrt(r2) * orc_lj_dr(r2, sys->eps[ta * sys->S + tb], sys->sigma[ta * sys->S + tb]);
     return u;
 }
@@ -523,7 +526,7 @@ static double pair_energy_w(const orc_sys *sys, const uint32_t A[3], int ta, con
 static double pair_energy(const orc_sys *sys, const uint32_t A[3], int ta, const uint32_t B[3],
                           int tb, double *uabs)
 {
-    return pair_energy_w(sys, A, ta, B, tb, uabs, NULL);
+    return pair_energy_w(sys, A, ta, B, tb, uabs, NULL, NULL);
 }
 
 /* Energy of a particle of species t at grid position P against every
@@ -547,11 +550,12 @@ double orc_energy_brute(const orc_sys *sys, const uint32_t P[3], int t, int excl
  * (Algorithms 6 and 7; Sec. 3.2: the home cell and its 26 neighbours).
  * T >= 3 makes the 27 cells distinct. */
 static double energy_cells_w(const orc_sys *sys, const uint32_t P[3], int t, int excl_s,
-                             int64_t excl_i, double *uabs, double *wsum)
+                             int64_t excl_i, double *uabs, double *wsum, double *sabs)
 {
     double e = 0.0;
     if (uabs) *uabs = 0.0;
     if (wsum) *wsum = 0.0;
+    if (sabs) *sabs = 0.0;
     int T = sys->T;
     int cx = cell_coord(P[0], T), cy = cell_coord(P[1], T), cz = cell_coord(P[2], T);
     for (int oz = -1; oz <= 1; ++oz)
@@ -562,7 +566,7 @@ static double energy_cells_w(const orc_sys *sys, const uint32_t P[3], int t, int
                 for (int64_t k = 0; k < sys->cell_len[c]; ++k) {
                     orc_ref r = sys->cell[c][k];
                     if (r.s == excl_s && r.i == excl_i) continue;
-                    e += pair_energy_w(sys, P, t, &sys->pos[r.s][3 * r.i], r.s, uabs, wsum);
+                    e += pair_energy_w(sys, P, t, &sys->pos[r.s][3 * r.i], r.s, uabs, wsum, sabs);
                 }
             }
     return e;
@@ -571,7 +575,7 @@ static double energy_cells_w(const orc_sys *sys, const uint32_t P[3], int t, int
 double orc_energy_cells(const orc_sys *sys, const uint32_t P[3], int t, int excl_s,
                         int64_t excl_i, double *uabs)
 {
-    return energy_cells_w(sys, P, t, excl_s, excl_i, uabs, NULL);
+    return energy_cells_w(sys, P, t, excl_s, excl_i, uabs, NULL, NULL);
 }
 
 /* Trial energies for m real positions (quantised by the grid rule).
@@ -787,9 +791,13 @@ void orc_move_words(uint64_t seed, uint64_t m, uint32_t chain, uint32_t w[8])
  * Alongside the energy the chain keeps the virial W = sum_{i<j} r U'(r) (the
  * pair sum behind the virial pressure P = rho k T - W / (3V), Sec. 3.1.2):
  * each trial's dW is the same 27-cell sum with r U'(r) in place of U.
+ * sum_abs_u (n_moves doubles, may be NULL) receives per move the sum of |u_j|
+ * over the pair terms the trial evaluated (both positions of a displacement),
+ * the floor of the per-move error measure |dU_a - dU_b| / max(|dU|, 1e-3
+ * sum_j |u_j|) by which two evaluations of a trial are compared.
  * Returns 0, or -1 when the energy is not set. */
-int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, int64_t n_moves,
-                  const orc_mix *mix, double tol, orc_trace *trace, orc_stats *st)
+int orc_run_moves_ex(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, int64_t n_moves,
+                     const orc_mix *mix, double tol, orc_trace *trace, orc_stats *st, double *sum_abs_u)
 {
     memset(st, 0, sizeof(*st));
     if (!(sys->E == sys->E)) return -1;
@@ -815,7 +823,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
         memset(&tr, 0, sizeof(tr));
         tr.type = (uint8_t)type;
         tr.index = -1;
-        double dU = 0.0, lnA = -INFINITY, uabs = 0.0, dW = 0.0;
+        double dU = 0.0, lnA = -INFINITY, uabs = 0.0, dW = 0.0, sabs = 0.0;
         int s = 0;
         int64_t i = -1;
         int possible = 1;
@@ -836,12 +844,13 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
                     int64_t step = (int64_t)(((uint64_t)w[2 + a] * span) >> 32) - D;
                     Pn[a] = (uint32_t)((int64_t)Po[a] + step);
                 }
-                double ua0 = 0.0, ua1 = 0.0, w0 = 0.0, w1 = 0.0;
-                double e_old = energy_cells_w(sys, Po, s, s, i, &ua0, &w0);
-                double e_new = energy_cells_w(sys, Pn, s, s, i, &ua1, &w1);
+                double ua0 = 0.0, ua1 = 0.0, w0 = 0.0, w1 = 0.0, sa0 = 0.0, sa1 = 0.0;
+                double e_old = energy_cells_w(sys, Po, s, s, i, &ua0, &w0, &sa0);
+                double e_new = energy_cells_w(sys, Pn, s, s, i, &ua1, &w1, &sa1);
                 dU = e_new - e_old;
                 dW = w1 - w0;
                 uabs = ua0 + ua1;
+                sabs = sa0 + sa1;
                 lnA = -mix->beta * dU;
             }
         } else if (type == 1) {
@@ -849,7 +858,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
             Pn[0] = w[2];
             Pn[1] = w[3];
             Pn[2] = w[4];
-            dU = energy_cells_w(sys, Pn, s, -1, -1, &uabs, &dW);
+            dU = energy_cells_w(sys, Pn, s, -1, -1, &uabs, &dW, &sabs);
             i = sys->n[s];
             lnA = mix->log_z[s] + lnV - log((double)(sys->n[s] + 1)) - mix->beta * dU;
         } else {
@@ -859,7 +868,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
             } else {
                 i = (int64_t)(((uint64_t)w[1] * (uint64_t)sys->n[s]) >> 32);
                 double w0 = 0.0;
-                dU = -energy_cells_w(sys, &sys->pos[s][3 * i], s, s, i, &uabs, &w0);
+                dU = -energy_cells_w(sys, &sys->pos[s][3 * i], s, s, i, &uabs, &w0, &sabs);
                 dW = -w0;
                 lnA = log((double)sys->n[s]) - mix->log_z[s] - lnV - mix->beta * dU;
             }
@@ -928,6 +937,7 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
             tr.flagged = (uint8_t)flag;
             trace[mm] = tr;
         }
+        if (sum_abs_u) sum_abs_u[mm] = sabs;
         int64_t Nn = 0;
         for (int q = 0; q < S; ++q) Nn += sys->n[q];
         st->sum_energy += sys->E;
@@ -939,6 +949,13 @@ int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, i
     st->virial = sys->W;
     for (int q = 0; q < S; ++q) st->n[q] = sys->n[q];
     return 0;
+}
+
+/* The chain without the per-move sums of |u_j|. */
+int orc_run_moves(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first, int64_t n_moves,
+                  const orc_mix *mix, double tol, orc_trace *trace, orc_stats *st)
+{
+    return orc_run_moves_ex(sys, seed, chain, first, n_moves, mix, tol, trace, st, NULL);
 }
 
 /* Current state: particle counts per species, grid positions in

@@ -264,3 +264,83 @@ def test_low_density_virial_matches_the_pair_integral():
     err = means.std(ddof=1) / math.sqrt(len(means))
     assert I > 0  # attraction (U' > 0 beyond the minimum) dominates at T* = 1.2: the pressure drops
     assert abs(means.mean() - want.mean()) < max(5 * err, 0.06 * abs(want.mean())), (means.mean(), want.mean(), err)
+
+
+def test_move_types_follow_the_mix():
+    """The attempted move types follow p_disp / p_ins / p_del (unequal here)
+    within a 6-sigma binomial bound; swapping two probabilities, or reading
+    the thresholds from the wrong side, moves a count by thousands of sigma."""
+    L = 8.0
+    s = O.System(L, 2.5, [[0.0]], [[1.0]])
+    s.build(W.uniform_positions(30, L, 3), np.zeros(30, np.int32))
+    s.set_energy(0.0)
+    p = (0.5, 0.3, 0.2)
+    n = 200_000
+    tr, st = s.run_moves(17, 0, n, *p, 0.3, 1.0, [math.log(0.05)])
+    for t in range(3):
+        cnt = int((tr["type"] == t).sum())
+        assert cnt == st.attempted[t]
+        sd = math.sqrt(n * p[t] * (1 - p[t]))
+        assert abs(cnt - n * p[t]) <= 6 * sd, (t, cnt)
+
+
+def test_displacement_steps_are_uniform_on_the_grid():
+    """An accepted displacement moves each coordinate by a whole number of grid
+    steps in [-D, D], D = floor(delta * 2^32 / L) (exact rational arithmetic
+    here), uniformly: the extreme steps are reached and a 10-bin histogram
+    of each axis passes a chi-square test.  Ideal gas, so every displacement
+    is accepted."""
+    from fractions import Fraction
+    L, delta = 8.0, 0.3
+    D = int(Fraction(delta) * (1 << 32) / Fraction(L))
+    s = O.System(L, 2.5, [[0.0]], [[1.0]])
+    n = 40
+    s.build(W.uniform_positions(n, L, 4), np.zeros(n, np.int32))
+    s.set_energy(0.0)
+    _, X0, _, _ = s.state()
+    steps = []
+    for m in range(3000):
+        tr, _ = s.run_moves(23, m, 1, 1.0, 0.0, 0.0, delta, 1.0, [0.0])
+        _, X1, _, _ = s.state()
+        i = int(tr["index"][0])
+        assert tr["accepted"][0] == 1
+        d = (X1[i].astype(np.int64) - X0[i].astype(np.int64) + (1 << 31)) % (1 << 32) - (1 << 31)
+        steps.append(d)
+        moved = np.ones(n, bool)
+        moved[i] = False
+        assert np.array_equal(X1[moved], X0[moved])
+        X0 = X1
+    steps = np.array(steps)
+    assert np.abs(steps).max() <= D
+    assert np.abs(steps).max() >= 0.99 * D
+    for ax in range(3):
+        h, _ = np.histogram(steps[:, ax], bins=10, range=(-D - 0.5, D + 0.5))
+        expect = len(steps) / 10
+        chi2 = ((h - expect) ** 2 / expect).sum()
+        assert chi2 < 33.7, (ax, h)  # 9 degrees of freedom, p = 1e-4
+
+
+def test_sum_abs_u_matches_textbook_brute_force():
+    """The per-move sum of |u_j| (the floor of the per-move error measure) of
+    insertion trials equals an independent numpy evaluation over all
+    particles at the trial's grid point (its Philox words 2-4)."""
+    L, rc = 7.5, 2.5
+    pos, types, eps, sigma = W.tiny_system(n=60, L=L, rc=rc, n_species=1, seed=5)
+    s = O.System(L, rc, eps, sigma)
+    s.build(pos, types)
+    s.set_energy(s.total_energy())
+    _, X, _, _ = s.state()
+    Xr = X.astype(np.float64) * (L / 2.0 ** 32)
+    tr, _, sabs = s.run_moves(31, 0, 200, 0.0, 1.0, 0.0, 0.3, 1e-9, [-50.0], with_sabs=True)
+    assert not tr["accepted"].any()
+    for m in range(200):
+        w = O.move_words(31, m)
+        P = w[2:5].astype(np.float64) * (L / 2.0 ** 32)
+        d = Xr - P
+        d -= L * np.rint(d / L)
+        r2 = (d * d).sum(1)
+        r2 = r2[r2 < rc * rc]
+        sr6 = (sigma[0, 0] ** 2 / r2) ** 3
+        want = np.abs(4 * eps[0, 0] * (sr6 * sr6 - sr6)).sum()
+        assert sabs[m] == pytest.approx(want, rel=1e-9, abs=1e-12)
+        assert abs(tr["dU"][m]) <= sabs[m] * (1 + 1e-12)

@@ -136,7 +136,8 @@ typedef struct gcmc_ctx gcmc_ctx;
 
 /* Creates a context for one box.  Copies the eps/sigma tables (Eq. 1) and
  * derives the cell grid of Sec. 3.2.2.  stream: a cudaStream_t or NULL.
- * Allocates nothing on the device until gcmc_build_cells.
+ * Allocates only a few words of device memory (status, running energy,
+ * counts) until gcmc_build_cells.
  * Errors: INVALID_ARG (L, rc, species, tables, precision), CUDA. */
 gcmc_status gcmc_create(const gcmc_params *params, void *stream, gcmc_ctx **out);
 
@@ -254,10 +255,11 @@ gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy);
 
 /* The same full-system energy, computed without allocating any memory.  The
  * paper has no counterpart; this call exists for callers that cannot
- * allocate device memory where they need the energy: code that runs while
- * a stream is being captured, code whose device memory is all owned by
- * another allocator or a fixed budget, and real-time loops that must not
- * enter the driver's allocator.  It calls no cudaMalloc, cudaFree or other
+ * allocate device memory where they need the energy: code whose device
+ * memory is all owned by another allocator or held to a fixed budget, and
+ * real-time loops that must not enter the driver's allocator (an allocation
+ * can block on the device or fail when memory runs short).  It calls no
+ * cudaMalloc, cudaFree or other
  * allocating routine: it reads the padded cell layout that gcmc_build_cells
  * and gcmc_run_moves keep current, and keeps its per-cell partial sums in a
  * static device array of GCMC_NOALLOC_MAX_CELLS doubles (1 MiB) built into
@@ -272,8 +274,9 @@ gcmc_status gcmc_total_energy(gcmc_ctx *ctx, double *energy);
  * device shares the one array: calls whose kernels overlap on the GPU (on
  * different streams, or from different contexts) race and give wrong
  * energies; serialise them.
- * Errors: INVALID_ARG (NULL or host energy pointer, more than
- * GCMC_NOALLOC_MAX_CELLS cells), STATE (cells not built), CUDA. */
+ * Errors: INVALID_ARG (NULL or host energy pointer, memory of another
+ * device, more than GCMC_NOALLOC_MAX_CELLS cells), STATE (cells not built),
+ * CUDA. */
 #define GCMC_NOALLOC_MAX_CELLS 131072
 gcmc_status gcmc_total_energy_noalloc(gcmc_ctx *ctx, double *energy);
 
@@ -363,6 +366,13 @@ gcmc_status gcmc_batch_destroy(gcmc_batch *batch);
  * failing chain's status (its context has the message); INVALID_ARG. */
 gcmc_status gcmc_batch_run_moves(gcmc_batch *batch, const uint64_t *seeds, uint64_t first_move, int64_t n_moves,
                                  const gcmc_move_mix *mixes, gcmc_move_stats *stats);
+
+/* Per-chain move records for the following gcmc_batch_run_moves calls:
+ * traces is a host array of n_chains device pointers, each NULL or room for
+ * the n_moves records (gcmc_trace, the format of gcmc_run_moves) of a call,
+ * written at [0, n_moves) of every call; traces = NULL stops the records.
+ * The batch keeps the pointers, not the memory.  Errors: INVALID_ARG. */
+gcmc_status gcmc_batch_set_traces(gcmc_batch *batch, gcmc_trace *const *traces);
 
 /* Sets the team shape (-1 automatic, -2 leave unchanged) and reports the
  * current one and the per-shape probe times in ms of the last tuning (the

@@ -87,6 +87,7 @@ SIGNATURES = {
     "gcmc_batch_create": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
     "gcmc_batch_destroy": (C.c_int, [_vp]),
     "gcmc_batch_run_moves": (C.c_int, [_vp, _vp, C.c_uint64, C.c_int64, _vp, _vp]),
+    "gcmc_batch_set_traces": (C.c_int, [_vp, _vp]),
     "gcmc_batch_config": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "gcmc_batch_launches": (C.c_int, [_vp, _vp]),
     "gcmc_batch_device_ms": (C.c_int, [_vp, C.POINTER(C.c_double)]),

@@ -225,7 +225,8 @@ constexpr int kGMax = 8;  // warps per evaluation team, at most
 struct Slot {  // evaluators -> committer, one per move in flight
     Trial t;                      // written by the team's warp 0
     uint4 last_val;               // the old cell's last entry (by the lane that met it)
-    float ph[kGMax], pu[kGMax];   // per-warp FP32 sums: dU, uabs
+    float ph[kGMax], pu[kGMax];   // per-warp FP32 sums: dU (high word), uabs
+    float pl[kGMax];              // per-warp FP32 sums: dU (low word)
     double pd[kGMax], pa[kGMax];  // per-warp FP64 sums: dU, uabs
     float pw[kGMax];              // per-warp FP32 virial change (virial runs)
     double pwd[kGMax];            // per-warp FP64 virial change (virial runs)
@@ -338,15 +339,18 @@ __device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, 
 
 // ---------------------------------------------------------------- the chain
 // VIR: the evaluations also sum the virial change dW of each trial.
+constexpr int kQ = 64;  // entries of an evaluator warp's queue of pair terms inside the cutoff
+
 template <bool F32, bool VIR>
 struct Chain {
     const ChainArgs &a;
     Shared &sh;
     uint16_t *cnt;
+    int4 *fq;  // kQ entries per evaluator warp (warps 1 .. EW)
     int lane, warp, T;
     uint32_t uT;
 
-    __device__ Chain(const ChainArgs &a_, Shared &sh_, uint16_t *cnt_) : a(a_), sh(sh_), cnt(cnt_)
+    __device__ Chain(const ChainArgs &a_, Shared &sh_, uint16_t *cnt_, int4 *fq_) : a(a_), sh(sh_), cnt(cnt_), fq(fq_)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
@@ -493,15 +497,15 @@ struct Chain {
     }
 
     // One item (a particle of a work cell) against the trial's old and/or new
-    // position, branch-free so that the items of a lane interleave: every
-    // pair term is computed and then masked by the cutoff test.  The cutoff
-    // is decided on the FP32 squared distance except inside a thin band
-    // around rc^2, where the exact integer squared distance decides.
+    // position.  The cutoff is screened on the FP32 squared distance, except
+    // inside a thin band around rc^2 where the exact integer squared distance
+    // decides; the pairs inside the cutoff join the warp's queue and are
+    // evaluated 32 at a time in compensated FP32 (lj_ff), so the warp spends
+    // the long pair term only on the ~15 % of items inside the cutoff.
     // Per-evaluation constants of the FP32 item: the pair table entry of a
-    // single-species chain and the band around rc^2 (registers, not shared
-    // memory, inside the item loop).
+    // single-species chain and the band around rc^2 (registers).
     struct ItemK {
-        float c4e, sig2, r2lo, r2hi;
+        float c4e, sig2, c4l, sil, r2lo, r2hi;
         bool single, vir;
     };
 
@@ -511,23 +515,72 @@ struct Chain {
         K.single = a.S == 1;
         K.c4e = a.ff.c4e[0];
         K.sig2 = a.ff.sig2[0];
+        K.c4l = a.ff.c4e_lo[0];
+        K.sil = a.ff.sig2_lo[0];
         K.r2lo = a.r2lo;
         K.r2hi = a.r2hi;
         K.vir = VIR;
         return K;
     }
 
+    // A warp's queue of pair terms inside the cutoff: entries (ex, ey, ez,
+    // pair index | 0x100 for a term that counts negatively), a ring of kQ.
+    struct FQ {
+        int4 *buf;
+        int head, n;
+    };
+    // Per-lane sums of the FP32 evaluation: dU as hi + lo, uabs, virial.
+    struct Acc32 {
+        float eh, el, mag, wac;
+    };
+
+    // Evaluates `count` (<= 32) queued terms, one per lane, and adds them.
+    __device__ __forceinline__ void drain(const FQ &Q, int count, const ItemK &K, Acc32 &A) const
+    {
+        if (lane < count) {
+            const int4 e = Q.buf[(Q.head + lane) & (kQ - 1)];
+            const int kk = e.w & 0xFF;
+            float ch = K.c4e, cl = K.c4l, sh2 = K.sig2, sl2 = K.sil;
+            if (!K.single) {
+                ch = a.ff.c4e[kk];
+                cl = a.ff.c4e_lo[kk];
+                sh2 = a.ff.sig2[kk];
+                sl2 = a.ff.sig2_lo[kk];
+            }
+            float uh, ul, m;
+            lj_ff(e.x, e.y, e.z, ch, cl, sh2, sl2, uh, ul, m);
+            const bool neg = (e.w & 0x100) != 0;
+            ff_acc(A.eh, A.el, neg ? -uh : uh, neg ? -ul : ul);
+            A.mag += m;
+            if (K.vir) {
+                const float w = -fmaf(3.f, m, 9.f * uh);  // r U'(r) = -12 rep + 6 att
+                A.wac += neg ? -w : w;
+            }
+        }
+    }
+
+    // Adds the lanes' entries (where `in`) to the queue; drains 32 when full.
+    __device__ __forceinline__ void push(FQ &Q, bool in, const int4 &ent, const ItemK &K, Acc32 &A) const
+    {
+        const unsigned bm = __ballot_sync(0xffffffffu, in);
+        if (bm == 0u) return;
+        if (in) Q.buf[(Q.head + Q.n + __popc(bm & ((1u << lane) - 1u))) & (kQ - 1)] = ent;
+        Q.n += __popc(bm);
+        if (Q.n >= 32) {
+            __syncwarp();
+            drain(Q, 32, K, A);
+            Q.head = (Q.head + 32) & (kQ - 1);
+            Q.n -= 32;
+            __syncwarp();
+        }
+    }
+
     template <int SIDES>
     __device__ __forceinline__ void item32(const Trial &t, const uint4 &q, bool valid, uint32_t fl,
-                                           const ItemK &K, float &acc, float &mag, float &wac) const
+                                           const ItemK &K, FQ &Q, Acc32 &A) const
     {
         const bool use = valid && (q.w != t.Po.w);
-        float c4e = K.c4e, sig2 = K.sig2;
-        if (!K.single) {
-            const int kk = (int)t.s * kMaxSpecies + (int)tag_species(q.w);
-            c4e = a.ff.c4e[kk];
-            sig2 = a.ff.sig2[kk];
-        }
+        const int kk = K.single ? 0 : (int)t.s * kMaxSpecies + (int)tag_species(q.w);
         // SIDES 1: the old position only (deletion); 2: the new only
         // (insertion); 3: both (displacement)
         const uint4 &P0 = (SIDES == 2) ? t.Pn : t.Po;
@@ -562,19 +615,8 @@ struct Chain {
                     in = g < a.R2;
                 }
             }
-            const float r2 = in ? r2f : 1e30f;
-            const float s2 = __fdividef(sig2, r2);
-            const float s6 = s2 * s2 * s2;
-            const float cs = c4e * s6;
-            float u = cs * (s6 - 1.f), m = cs * (s6 + 1.f);
-            if (r2f == 0.f) u = m = __int_as_float(0x7f800000);  // r = 0 (every separation exactly 0)
             const bool neg = (SIDES == 1) || (SIDES == 3 && side == 0);
-            acc += in ? (neg ? -u : u) : 0.f;
-            mag += in ? m : 0.f;
-            if (K.vir) {
-                const float w = -fmaf(3.f, m, 9.f * u);  // r U'(r) = -12 rep + 6 att
-                wac += in ? (neg ? -w : w) : 0.f;
-            }
+            push(Q, in, make_int4(ex, ey, ez, kk | (neg ? 0x100 : 0)), K, A);
         }
     }
 
@@ -587,7 +629,7 @@ struct Chain {
     // them, the trial particle's slot in its old cell and that cell's last
     // entry.
     struct Part {
-        float e, ua, w;
+        float e, el, ua, w;  // FP32 runs: dU = e + el
         double de, da, dw;
         int self_slot, has_last;
         int seq;  // count epoch of the work-cell counts this warp read, -1 if a change tore them
@@ -596,13 +638,12 @@ struct Chain {
 
     template <bool P32>
     __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, const ItemK &K,
-                                         float &acc, float &mag, float &wac, double &de, double &da,
-                                         double &dw) const
+                                         FQ &Q, Acc32 &A, double &de, double &da, double &dw) const
     {
         if constexpr (P32) {
-            if (t.type == 0) item32<3>(t, q, valid, fl, K, acc, mag, wac);
-            else if (t.type == 1) item32<2>(t, q, valid, fl, K, acc, mag, wac);
-            else item32<1>(t, q, valid, fl, K, acc, mag, wac);
+            if (t.type == 0) item32<3>(t, q, valid, fl, K, Q, A);
+            else if (t.type == 1) item32<2>(t, q, valid, fl, K, Q, A);
+            else item32<1>(t, q, valid, fl, K, Q, A);
         } else if (valid && q.w != t.Po.w) {
             FF e0 = {0.f, 0.f};
             float u0 = 0.f;
@@ -619,7 +660,8 @@ struct Chain {
         o.self_slot = -1;
         o.has_last = 0;
         o.last = make_uint4(0, 0, 0, 0);
-        float acc = 0.f, mag = 0.f, wac = 0.f;
+        Acc32 A = {0.f, 0.f, 0.f, 0.f};
+        FQ Q = {P32 ? fq + (warp - 1) * kQ : nullptr, 0, 0};
         double de = 0.0, da = 0.0, dw = 0.0;
         const int nw = nwork(t);
         AxisList X, Y, Z;
@@ -697,18 +739,22 @@ struct Chain {
                         o.last = q[u];
                     }
                 }
-                item<P32>(t, q[u], v, flg[u], K, acc, mag, wac, de, da, dw);
+                item<P32>(t, q[u], v, flg[u], K, Q, A, de, da, dw);
             }
         }
         o.w = 0.f;
         o.dw = 0.0;
         if constexpr (P32) {
-            o.e = warp_sum(acc);
-            o.ua = warp_sum(mag);
-            if (K.vir) o.w = warp_sum(wac);
+            if (Q.n > 0) drain(Q, Q.n, K, A);
+            __syncwarp();
+            const FF e = ff_warp_sum(FF{A.eh, A.el});
+            o.e = e.hi;
+            o.el = e.lo;
+            o.ua = warp_sum(A.mag);
+            if (K.vir) o.w = warp_sum(A.wac);
             o.de = o.da = 0.0;
         } else {
-            o.e = o.ua = 0.f;
+            o.e = o.el = o.ua = 0.f;
             o.de = warp_sum(de);
             o.da = warp_sum(da);
             if (K.vir) o.dw = warp_sum(dw);
@@ -1013,7 +1059,9 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         }
         return;
     }
-    Chain<F32, VIR> C(a, sh, cnt);
+    // the evaluator warps' queues of pair terms (FP32 runs)
+    __shared__ int4 fq[F32 ? EW * kQ : 1];
+    Chain<F32, VIR> C(a, sh, cnt, fq);
     const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
     const int n = a.n_moves;
     const int keeper_warp = EW + 1;
@@ -1171,6 +1219,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 S.pseq[j] = P.seq;
                 if constexpr (F32) {
                     S.ph[j] = P.e;
+                    S.pl[j] = P.el;
                     S.pu[j] = P.ua;
                     S.pw[j] = P.w;
                 } else {
@@ -1260,7 +1309,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             float uab = 0.f;
             double de = 0.0, da = 0.0, dW = 0.0;
             if constexpr (F32) {
-                FF v = {lane < G ? S.ph[lane] : 0.f, 0.f};
+                FF v = {lane < G ? S.ph[lane] : 0.f, lane < G ? S.pl[lane] : 0.f};
                 float u = lane < G ? S.pu[lane] : 0.f;
                 float w = (VIR && lane < G) ? S.pw[lane] : 0.f;
 #pragma unroll
@@ -1863,7 +1912,10 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
 static gcmc_status check_chain_fits(gcmc_ctx *ctx)
 {
     const size_t smem = ((size_t)ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16;
-    if (smem + sizeof(Shared) + sizeof(ChainArgs) + 4096 > ctx->smem_optin)
+    // static shared memory: the chain state, its arguments, the evaluator
+    // warps' pair-term queues (at most 14 warps) and a margin for the rest
+    const size_t queues = 14 * kQ * sizeof(int4);
+    if (smem + sizeof(Shared) + sizeof(ChainArgs) + queues + 4096 > ctx->smem_optin)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: too many cells for the on-chip cell counters");
     if (ctx->T > 1023) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: more than 1023 cells per side");
     return GCMC_OK;
@@ -1909,7 +1961,8 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
 
 gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
-                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms, double *dev_ms)
+                      std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms, double *dev_ms,
+                      gcmc_trace *const *traces)
 {
     if (dev_ms) *dev_ms = 0.0;
     if (K <= 0) return GCMC_OK;
@@ -1962,6 +2015,7 @@ gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint6
         j.first = first;
         j.n_moves = n_moves;
         j.mix = mixes[k];
+        j.trace = traces ? traces[k] : nullptr;
         j.result = GCMC_OK;
         const bool vir = (mixes[k].flags & GCMC_MIX_VIRIAL) != 0;
         j.agg.virial = vir ? ctxs[k]->virial : NAN;

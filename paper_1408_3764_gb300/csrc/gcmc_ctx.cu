@@ -150,6 +150,8 @@ gcmc_status gcmc_create(const gcmc_params *p, void *stream, gcmc_ctx **out)
             ctx->fd.sig2[a * kMaxSpecies + b] = sg * sg;
             ctx->ff.c4e[a * kMaxSpecies + b] = (float)(4.0 * e);
             ctx->ff.sig2[a * kMaxSpecies + b] = (float)(sg * sg);
+            ctx->ff.c4e_lo[a * kMaxSpecies + b] = (float)(4.0 * e - (double)(float)(4.0 * e));
+            ctx->ff.sig2_lo[a * kMaxSpecies + b] = (float)(sg * sg - (double)(float)(sg * sg));
         }
     ctx->max_particles_req = p->max_particles;
     ctx->cap_req = p->cell_capacity;
@@ -451,7 +453,7 @@ gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const ui
         N += n_per_species[s];
         if (n_per_species[s] > nmax) nmax = n_per_species[s];
     }
-    if (N > 0 && (!pos_grid || !cell_count || !cell_refs))
+    if (!cell_count || (N > 0 && (!pos_grid || !cell_refs)))
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_set_state: NULL arrays");
     // validate the cell list against the positions
     int64_t tot = 0, maxc = 0;
@@ -487,51 +489,66 @@ gcmc_status gcmc_set_state(gcmc_ctx *ctx, const int64_t *n_per_species, const ui
     int64_t want_maxN = ctx->max_particles_req > 0 ? ctx->max_particles_req
                                                     : std::max<int64_t>(1024, 2 * nmax);
     if (nmax > want_maxN) return fail(ctx, GCMC_ERR_CAPACITY, "gcmc_set_state: above max_particles");
-    int want_cap = ctx->cap_req > 0 ? ctx->cap_req : (int)(((maxc * 5 / 4 + 8) + 7) / 8 * 8);
-    if (want_cap < 8) want_cap = 8;
-    if (maxc > want_cap) return fail(ctx, GCMC_ERR_CELL_OVERFLOW, "gcmc_set_state: cell too full");
+    const int64_t want_cap64 = ctx->cap_req > 0 ? ctx->cap_req : ((maxc * 5 / 4 + 8) + 7) / 8 * 8;
+    if (maxc > want_cap64 || want_cap64 > 65535)  // the chain keeps cell counts as 16-bit words
+        return fail(ctx, GCMC_ERR_CELL_OVERFLOW, "gcmc_set_state: cell too full");
+    const int want_cap = std::max<int>(8, (int)want_cap64);
+    // the new arrays first: a refused allocation leaves the old configuration as it was
+    uint4 *ncp = nullptr, *npb = nullptr;
+    int32_t *ncc = nullptr;
+    cudaError_t e = cudaMalloc(&ncp, (size_t)ctx->ncell * want_cap * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&ncc, (size_t)ctx->ncell * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&npb, (size_t)S * want_maxN * sizeof(uint4));
+    std::vector<uint4> cp, pb;
+    if (e == cudaSuccess) {
+        cp.assign((size_t)ctx->ncell * want_cap, make_uint4(0, 0, 0, 0));
+        pb.assign((size_t)S * want_maxN, make_uint4(0, 0, 0, 0));
+        int64_t k = 0;
+        for (int64_t c = 0; c < ctx->ncell; ++c)
+            for (int j = 0; j < cell_count[c]; ++j, ++k) {
+                const uint32_t r = cell_refs[k];
+                const int s = (int)(r & 0xFF);
+                const int64_t row = base[s] + (r >> 8);
+                const uint4 v = make_uint4(pos_grid[3 * row], pos_grid[3 * row + 1], pos_grid[3 * row + 2], r);
+                cp[(size_t)c * want_cap + j] = v;
+                pb[(size_t)s * want_maxN + (r >> 8)] = v;
+            }
+        e = cudaMemcpy(ncp, cp.data(), cp.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ncc, cell_count, ctx->ncell * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(npb, pb.data(), pb.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(ncp);
+        cudaFree(ncc);
+        cudaFree(npb);
+        return cuda_fail(ctx, e, "gcmc_set_state: new configuration arrays");
+    }
     if (ctx->cell_pos) cudaFree(ctx->cell_pos);
     if (ctx->cell_count) cudaFree(ctx->cell_count);
     if (ctx->pos_by_id) cudaFree(ctx->pos_by_id);
-    ctx->cell_pos = nullptr;
-    ctx->cell_count = nullptr;
-    ctx->pos_by_id = nullptr;
+    ctx->cell_pos = ncp;
+    ctx->cell_count = ncc;
+    ctx->pos_by_id = npb;
     ctx->maxN = want_maxN;
     ctx->cap = want_cap;
-    GCMC_CUDA(ctx, cudaMalloc(&ctx->cell_pos, (size_t)ctx->ncell * ctx->cap * sizeof(uint4)));
-    GCMC_CUDA(ctx, cudaMalloc(&ctx->cell_count, (size_t)ctx->ncell * sizeof(int32_t)));
-    GCMC_CUDA(ctx, cudaMalloc(&ctx->pos_by_id, (size_t)S * ctx->maxN * sizeof(uint4)));
-    std::vector<uint4> cp((size_t)ctx->ncell * ctx->cap, make_uint4(0, 0, 0, 0));
-    std::vector<uint4> pb((size_t)S * ctx->maxN, make_uint4(0, 0, 0, 0));
-    int64_t k = 0;
-    for (int64_t c = 0; c < ctx->ncell; ++c)
-        for (int j = 0; j < cell_count[c]; ++j, ++k) {
-            const uint32_t r = cell_refs[k];
-            const int s = (int)(r & 0xFF);
-            const int64_t row = base[s] + (r >> 8);
-            const uint4 v = make_uint4(pos_grid[3 * row], pos_grid[3 * row + 1], pos_grid[3 * row + 2], r);
-            cp[(size_t)c * ctx->cap + j] = v;
-            pb[(size_t)s * ctx->maxN + (r >> 8)] = v;
-        }
-    GCMC_CUDA(ctx, cudaMemcpy(ctx->cell_pos, cp.data(), cp.size() * sizeof(uint4), cudaMemcpyHostToDevice));
-    GCMC_CUDA(ctx, cudaMemcpy(ctx->cell_count, cell_count, ctx->ncell * sizeof(int32_t),
-                              cudaMemcpyHostToDevice));
-    GCMC_CUDA(ctx, cudaMemcpy(ctx->pos_by_id, pb.data(), pb.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    // nothing derived from the old configuration stays valid
+    ctx->built = false;
+    ctx->compact_valid = false;
+    ctx->order_valid = false;
+    ctx->energy_valid = false;
+    ctx->virial_valid = false;
+    ctx->mc_valid = false;
     int64_t nn[kMaxSpecies] = {0};
     for (int s = 0; s < S; ++s) nn[s] = n_per_species[s];
     GCMC_CUDA(ctx, cudaMemcpy(ctx->d_n, nn, sizeof(nn), cudaMemcpyHostToDevice));
     for (int s = 0; s < kMaxSpecies; ++s) ctx->n_host[s] = nn[s];
     GCMC_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
     ctx->built = true;
-    ctx->compact_valid = false;
-    ctx->order_valid = false;
     ctx->n_build = N;
+    if (!std::isnan(energy)) GCMC_CUDA(ctx, cudaMemcpy(ctx->d_energy, &energy, sizeof(double), cudaMemcpyHostToDevice));
     ctx->energy = energy;
     ctx->energy_valid = !std::isnan(energy);
-    ctx->virial_valid = false;
-    ctx->mc_valid = false;
-    if (ctx->energy_valid)
-        GCMC_CUDA(ctx, cudaMemcpy(ctx->d_energy, &ctx->energy, sizeof(double), cudaMemcpyHostToDevice));
     return GCMC_OK;
 }
 
@@ -596,6 +613,7 @@ struct gcmc_batch {
     int64_t launches = 0;
     double probe_ms[kChainConfigs] = {};
     double last_ms = 0.0;  // device time of the last call's chain launches
+    std::vector<gcmc_trace *> traces;  // per chain, device, or empty: no traces
     std::string err;
 };
 
@@ -654,9 +672,21 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
     for (gcmc_ctx *c : b->ctxs) c->mc_valid = false;  // the batched chain keeps the 27-cell lists only
     std::string err;
     gcmc_status st = run_batch(b->ctxs.data(), (int)b->ctxs.size(), seeds, first_move, n_moves, mixes, stats,
-                               b->config, &b->launches, &err, b->stream, true, b->probe_ms, &b->last_ms);
+                               b->config, &b->launches, &err, b->stream, true, b->probe_ms, &b->last_ms,
+                               b->traces.empty() ? nullptr : b->traces.data());
     if (st != GCMC_OK) b->err = err.empty() ? "gcmc_batch_run_moves: a chain failed (see its context)" : err;
     return st;
+}
+
+gcmc_status gcmc_batch_set_traces(gcmc_batch *b, gcmc_trace *const *traces)
+{
+    if (!b) return GCMC_ERR_INVALID_ARG;
+    if (!traces) {
+        b->traces.clear();
+        return GCMC_OK;
+    }
+    b->traces.assign(traces, traces + b->ctxs.size());
+    return GCMC_OK;
 }
 
 gcmc_status gcmc_batch_config(gcmc_batch *b, int32_t set_config, int32_t *config_out, double *probe_ms)

@@ -125,7 +125,7 @@ void micro_free(gcmc_ctx *ctx);
 gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint64_t first, int64_t n_moves,
                       const gcmc_move_mix *mixes, gcmc_move_stats *stats, int &config, int64_t *launches,
                       std::string *err, cudaStream_t stream, bool use_graph, double *probe_ms,
-                      double *dev_ms);
+                      double *dev_ms, gcmc_trace *const *traces = nullptr);
 int chain_threads(int config);
 constexpr int kChainConfigs = 4;
 

@@ -111,6 +111,10 @@ __device__ __forceinline__ GridSep grid_sep(uint4 a, uint4 b)
 struct FieldF {
     float c4e[kMaxSpecies * kMaxSpecies];
     float sig2[kMaxSpecies * kMaxSpecies];
+    // the rounding residues: c4e + c4e_lo and sig2 + sig2_lo are the FP64
+    // constants to about 2^-48 (the compensated pair term below uses them)
+    float c4e_lo[kMaxSpecies * kMaxSpecies];
+    float sig2_lo[kMaxSpecies * kMaxSpecies];
 };
 struct FieldD {
     double c4e[kMaxSpecies * kMaxSpecies];
@@ -133,6 +137,75 @@ __device__ __forceinline__ void lj_f32(const GridSep &s, float c4e, float sig2, 
         u = __int_as_float(0x7f800000);
         mag = u;
     }
+}
+
+// Compensated FP32 pair energy (float-float, after Dekker's double-length
+// arithmetic, Numer. Math. 18 (1971): a value is an unevaluated sum hi + lo
+// of two floats; TwoProduct takes the exact rounding error of a product with
+// one FMA, TwoSum (Knuth) the exact error of a sum).  From the exact integer
+// separation (ex, ey, ez) of a pair inside the cutoff:
+//   r^2 = g exactly as an integer, split into r2h + r2l;
+//   s^2 = sig2 / r^2: an approximate quotient q corrected by its residual;
+//   s^6 = (s^2)^3, t = s^6 - 1, v = s^6 t, U = c4e v, each step keeping its
+//   rounding error in the low word.
+// Every operation is FP32 (the FP32 pipe); the result uh + ul carries a
+// relative error near 1e-13 of rep + att, where a plain FP32 evaluation
+// carries about 1e-6.  m = rep + att in plain FP32 (an error scale only).
+// g == 0 (both particles on one grid point) gives U = +inf.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void lj_ff(int ex, int ey, int ez, float ch, float cl, float sh, float sl, float &uh,
+                                      float &ul, float &m)
+{
+    const unsigned long long g = (unsigned long long)((long long)ex * ex) +
+                                 (unsigned long long)((long long)ey * ey) +
+                                 (unsigned long long)((long long)ez * ez);
+    if (g == 0ull) {
+        uh = __int_as_float(0x7f800000);
+        ul = 0.f;
+        m = uh;
+        return;
+    }
+    const float r2h = __ull2float_rn(g);
+    const float r2l = __ll2float_rn((long long)(g - __float2ull_rz(r2h)));
+    const float rcp = rcp_approx(r2h);
+    // s^2 = q + ql: the residual (sh + sl) - q (r2h + r2l) divided by r^2
+    const float q = __fmul_rn(sh, rcp);
+    float res = fmaf(-q, r2h, sh);
+    res = fmaf(-q, r2l, __fadd_rn(res, sl));
+    const float ql = __fmul_rn(res, rcp);
+    // s^6 = (q + ql)^3 = q^3 + 3 q^2 ql + ...: the two products exactly
+    const float a = __fmul_rn(q, q), ae = fmaf(q, q, -a);
+    const float b = __fmul_rn(a, q), be = fmaf(a, q, -b);
+    const float s6l = fmaf(__fmul_rn(3.f, a), ql, fmaf(ae, q, be));
+    // t = s^6 - 1 (TwoSum of b and -1)
+    const float t = __fadd_rn(b, -1.f);
+    const float bb = __fsub_rn(t, b);
+    const float te = __fadd_rn(__fsub_rn(b, __fsub_rn(t, bb)), __fsub_rn(-1.f, bb));
+    const float tl = __fadd_rn(te, s6l);
+    // v = s^6 (s^6 - 1)
+    const float vh = __fmul_rn(b, t);
+    const float vl = fmaf(b, tl, fmaf(s6l, t, fmaf(b, t, -vh)));
+    // U = c4e v
+    uh = __fmul_rn(ch, vh);
+    ul = fmaf(ch, vl, fmaf(cl, vh, fmaf(ch, vh, -uh)));
+    m = ch * b * (b + 1.f);
+}
+
+// hi + lo += x_hi + x_lo for a running sum of few terms: TwoSum on the high
+// words, the low words and the error summed in FP32.
+__device__ __forceinline__ void ff_acc(float &hi, float &lo, float xh, float xl)
+{
+    const float s = __fadd_rn(hi, xh);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(xh, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, xl));
 }
 
 __device__ __forceinline__ void lj_f64(const GridSep &s, double c4e, double sig2, double &u,

@@ -532,11 +532,10 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
 
 // ---------------------------------------------------------------------------
 // Allocation-free full-system energy.  Some callers may not allocate device
-// memory at the point where they need the energy: code running while a
-// stream is being captured into a CUDA graph (where cudaMalloc is not
-// allowed or not wanted), code under a fixed device-memory budget owned by
-// another allocator, or a real-time loop that must not enter the driver's
-// allocator.  This variant reads the padded cell layout that the chain keeps
+// memory at the point where they need the energy: code under a fixed
+// device-memory budget owned by another allocator, or a real-time loop that
+// must not enter the driver's allocator (which can block or fail when memory
+// runs short).  This variant reads the padded cell layout that the chain keeps
 // current (so no compact copy has to be built or grown) and keeps its
 // per-cell partial sums in one file-scope device array instead of the
 // context's scratch.  The array is shared by every call on a device: two
@@ -655,6 +654,10 @@ static gcmc_status total_energy_noalloc_on_device(gcmc_ctx *ctx, double *energy_
     GCMC_CUDA(ctx, cudaPointerGetAttributes(&attr, energy_dev));
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_total_energy_noalloc: energy must be device memory");
+    if (attr.type == cudaMemoryTypeDevice && attr.device != ctx->device)
+        return fail(ctx, GCMC_ERR_INVALID_ARG,
+                    "gcmc_total_energy_noalloc: energy is memory of device " + std::to_string(attr.device) +
+                        ", the context's device is " + std::to_string(ctx->device));
     double *partial = nullptr;
     gcmc_status st = static_partials(ctx, ctx->device, &partial);
     if (st != GCMC_OK) return st;

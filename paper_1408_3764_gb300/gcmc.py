@@ -323,17 +323,33 @@ class Batch:
         except Exception:
             pass
 
-    def run_moves(self, seeds, first_move: int, n_moves: int, mixes: Sequence[Mix], check_status=True):
-        """Moves first_move .. first_move + n_moves - 1 of every chain in one launch; per-chain statistics."""
+    def run_moves(self, seeds, first_move: int, n_moves: int, mixes: Sequence[Mix], check_status=True,
+                  trace: bool = False):
+        """Moves first_move .. first_move + n_moves - 1 of every chain in one launch; per-chain
+        statistics (and with trace=True the per-chain move records, as Box.run_moves gives them)."""
         K = len(self.boxes)
         sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(K))
         cm = (MoveMix * K)(*[m.to_c() for m in mixes])
         st = (MoveStats * K)()
-        rc = self._lib.gcmc_batch_run_moves(self._h, sd.ctypes.data_as(C.c_void_p), int(first_move),
-                                            int(n_moves), cm, st)
+        bufs = None
+        if trace:
+            dev = self.boxes[0].device
+            bufs = [torch.empty((max(n_moves, 1), _lib.TRACE_BYTES), dtype=torch.uint8, device=dev)
+                    for _ in range(K)]
+            arr = (C.c_void_p * K)(*[t.data_ptr() for t in bufs])
+            check(self._lib.gcmc_batch_set_traces(self._h, arr), None, "gcmc_batch_set_traces")
+        try:
+            rc = self._lib.gcmc_batch_run_moves(self._h, sd.ctypes.data_as(C.c_void_p), int(first_move),
+                                                int(n_moves), cm, st)
+        finally:
+            if trace:
+                self._lib.gcmc_batch_set_traces(self._h, None)
         if check_status and rc != 0:
             raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
-        return [stats_dict(st[k], self.boxes[k].S) for k in range(K)]
+        stats = [stats_dict(st[k], self.boxes[k].S) for k in range(K)]
+        if trace:
+            return stats, [b[:n_moves].cpu().numpy().copy().view(TRACE_DTYPE).reshape(-1) for b in bufs]
+        return stats
 
     def config(self, set_config: int = -2):
         """Sets the team shape (-1 automatic, -2 unchanged); returns it and the tuner's per-shape times."""

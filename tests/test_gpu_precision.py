@@ -1,0 +1,282 @@
+"""GPU precision against the FP64 oracle, at the stated workload sizes.
+
+The per-move energy-change error is measured as
+    err = |dU_gpu - dU_oracle| / max(|dU_oracle|, 1e-3 * sum_j |u_j|),
+sum_j |u_j| being the oracle's sum of the magnitudes of the pair terms the
+trial evaluates (both positions of a displacement): a relative error that
+stays meaningful when dU is near zero.  The FP32 mode must keep err <= 1e-5
+on every move (its pair terms are evaluated in compensated FP32); the FP64
+mode is held to 1e-12 on all but the moves where the two FP64 evaluations
+themselves differ in the last bits of terms much larger than dU (bounded at
+2e-11, the fraction above 1e-12 is reported).
+
+Also here: the million-particle mixture's full-system energy against the
+oracle, the 262,144-particle gradient on a 512-particle subset against the
+oracle's analytic gradient and against central differences, and the energy
+drift of the 131,072-particle chain over 10^6 moves.
+"""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_1408_3764_gb300 import workloads as W  # noqa: E402
+from paper_1408_3764_gb300.gcmc import Batch, Box, Mix, species_major_order  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def du_errors(tg, to, sabs):
+    """Per-move err of the GPU trace against the oracle's (moves before the
+    first decision that differs; moves whose trial was impossible are 0)."""
+    n = len(to)
+    same = np.ones(n, bool)
+    for k in ("type", "species", "index", "accepted"):
+        same &= tg[k] == to[k]
+    stop = n if same.all() else int(np.argmin(same))
+    tg, to, sabs = tg[:stop], to[:stop], sabs[:stop]
+    ok = np.isfinite(to["lnA"]) & np.isfinite(to["dU"])
+    den = np.maximum(np.abs(to["dU"]), 1e-3 * sabs)
+    err = np.zeros(stop)
+    nz = ok & (den > 0)
+    err[nz] = np.abs(tg["dU"][nz] - to["dU"][nz]) / den[nz]
+    # no pair inside the cutoff: both sides must give exactly zero
+    assert np.all(tg["dU"][ok & (den == 0)] == 0.0)
+    return err, stop
+
+
+def _chain_pair(w, precision):
+    o = O.System(w.L, w.rc, w.eps, w.sigma)
+    o.build(w.positions(), w.types())
+    o.set_energy(o.total_energy())
+    b = Box(w.L, w.rc, w.eps, w.sigma, precision=precision)
+    b.build_cells(torch.as_tensor(w.positions()), torch.as_tensor(w.types()))
+    return o, b
+
+
+def _mixargs(w):
+    return (w.p_disp, w.p_ins, w.p_del, w.max_disp, w.beta, w.log_z)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_du_error_plain_2048(precision):
+    """2,048 particles, rho 0.5, 10^4 moves (seed 1): every move's dU error."""
+    w = W.c1_plain_fp64()
+    o, b = _chain_pair(w, precision)
+    to, _, sabs = o.run_moves(w.seed, 0, w.moves, *_mixargs(w), tol=TOL[precision], with_sabs=True)
+    _, tg = b.run_moves(w.seed, 0, w.moves, Mix(*_mixargs(w)), trace=True)
+    err, stop = du_errors(tg, to, sabs)
+    assert stop == w.moves
+    if precision == "fp32":
+        assert err.max() <= 1e-5, err.max()
+    else:
+        assert err.max() <= 2e-11, err.max()
+        assert (err > 1e-12).mean() <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_du_error_and_drift_131072_one_million_moves(precision):
+    """131,072 particles, rho 0.6, rc 3: 10^5 moves relax the uniform start,
+    both sides recompute the total energy, then 10^6 moves are compared move
+    by move.  Drift = running energy after the moves minus the oracle's
+    full-system energy of the final configuration."""
+    w = W.c2_fp32_vs_fp64()
+    o, b = _chain_pair(w, precision)
+    mix = Mix(*_mixargs(w))
+    relax, n = 100_000, 1_000_000
+    o.run_moves(w.seed, 0, relax, *_mixargs(w), tol=TOL[precision], trace=False)
+    b.run_moves(w.seed, 0, relax, mix)
+    o.set_energy(o.total_energy())
+    e0 = b.total_energy()
+    assert abs(e0 - o.energy()) <= TOL[precision] * abs(o.energy())
+    # the drift measures the chain alone: both running energies start from
+    # the oracle's FP64 full-system energy of the relaxed configuration
+    b.restore(*b.get_state()[:4], energy=o.energy())
+    to, so, sabs = o.run_moves(w.seed, relax, n, *_mixargs(w), tol=TOL[precision], with_sabs=True)
+    sg, tg = b.run_moves(w.seed, relax, n, mix, trace=True)
+    err, stop = du_errors(tg, to, sabs)
+    assert stop == n
+    if precision == "fp32":
+        assert err.max() <= 1e-5, err.max()
+    else:
+        assert err.max() <= 2e-11, err.max()
+        assert (err > 1e-12).mean() <= 1e-3
+    # same final configuration; the drift of the running energy
+    st_o, st_g = o.state(), b.get_state()
+    for x, y in zip(st_o, st_g[:4]):
+        assert np.array_equal(x, y)
+    e_final = o.total_energy()
+    drift = sg["energy"] - e_final
+    assert abs(so.energy - e_final) <= 1e-9 * abs(e_final) + 1e-6 * to["uabs"][to["accepted"] == 1].max()
+    # each accepted dU carries at most ~1e-12 relative to its pair terms
+    bound = 1e-10 * to["uabs"][to["accepted"] == 1].sum() + 1e-9 * abs(e_final)
+    assert abs(drift) <= bound, (drift, bound)
+
+
+def test_du_error_isotherm_64_chains():
+    """The batched isotherm as the benchmark runs it (64 chains, one launch,
+    FP32 pair terms), 20,000 moves per chain: every chain equals the oracle's
+    chain k move for move, and every move's dU error is <= 1e-5."""
+    chains = W.isotherm_chains()
+    boxes, mixes, seeds = [], [], []
+    for k, w in enumerate(chains):
+        b = Box(w.L, w.rc, w.eps, w.sigma, precision="fp32")
+        b.build_cells(torch.as_tensor(w.positions()), torch.as_tensor(w.types()))
+        boxes.append(b)
+        mixes.append(Mix(*_mixargs(w)))
+        seeds.append(w.seed)
+    n = 20_000
+    batch = Batch(boxes)
+    stats, traces = batch.run_moves(seeds, 0, n, mixes, trace=True)
+    assert all(s["moves_done"] == n for s in stats)
+
+    def oracle_chain(k):
+        w = chains[k]
+        o = O.System(w.L, w.rc, w.eps, w.sigma)
+        o.build(w.positions(), w.types())
+        o.set_energy(o.total_energy())
+        to, so, sabs = o.run_moves(w.seed, 0, n, *_mixargs(w), tol=1e-5, chain=k, with_sabs=True)
+        return to, so, sabs, o.state()
+
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:  # the oracle's C calls release the GIL
+        refs = list(ex.map(oracle_chain, range(len(chains))))
+    worst = 0.0
+    for k, (to, so, sabs, st_o) in enumerate(refs):
+        err, stop = du_errors(traces[k], to, sabs)
+        assert stop == n, k
+        worst = max(worst, float(err.max()))
+        assert stats[k]["accepted"] == list(so.accepted), k
+        st_g = boxes[k].get_state()
+        for x, y in zip(st_o, st_g[:4]):
+            assert np.array_equal(x, y), k
+        assert abs(stats[k]["energy"] - so.energy) <= 1e-10 * to["uabs"].sum() + 1e-9
+    assert worst <= 1e-5, worst
+
+
+def test_total_energy_mixture_1m():
+    """The million-particle two-species mixture: full-system energy in both
+    precisions against the oracle, within tol * (1/2 sum over particles of
+    uabs)."""
+    w = W.c3_mixture_1m()
+    o = O.System(w.L, w.rc, w.eps, w.sigma)
+    o.build(w.positions(), w.types())
+    ref = o.total_energy()
+    scale = _half_uabs(o, w)
+    for precision in ("fp64", "fp32"):
+        b = Box(w.L, w.rc, w.eps, w.sigma, precision=precision)
+        b.build_cells(torch.as_tensor(w.positions()), torch.as_tensor(w.types()))
+        got = b.total_energy()
+        assert abs(got - ref) <= TOL[precision] * scale, (precision, got, ref, scale)
+        b.close()
+
+
+def _half_uabs(o, w):
+    """1/2 sum over particles of the uabs of their 27-cell energies."""
+    types = w.types()
+    sm = species_major_order(types)
+    cnt = o.counts()
+    pos = w.positions()[sm]
+    ts = types[sm]
+    ex = np.empty(len(sm), np.int64)
+    start = 0
+    for s in range(len(cnt)):
+        ex[start:start + cnt[s]] = (s << 32) | np.arange(cnt[s], dtype=np.int64)
+        start += cnt[s]
+    parts = np.array_split(np.arange(len(sm)), 16)
+
+    def part(ix):
+        return o.trial_energy(pos[ix], ts[ix], exclude=ex[ix], with_abs=True)[1].sum()
+
+    with cf.ThreadPoolExecutor(max_workers=16) as pool:
+        return 0.5 * sum(pool.map(part, parts))
+
+
+def test_total_energy_131072_within_uabs():
+    """The 131,072-particle workload: full-system energy within tol * (1/2 sum uabs)."""
+    w = W.c2_fp32_vs_fp64()
+    o = O.System(w.L, w.rc, w.eps, w.sigma)
+    o.build(w.positions(), w.types())
+    ref = o.total_energy()
+    scale = _half_uabs(o, w)
+    for precision in ("fp64", "fp32"):
+        b = Box(w.L, w.rc, w.eps, w.sigma, precision=precision)
+        b.build_cells(torch.as_tensor(w.positions()), torch.as_tensor(w.types()))
+        got = b.total_energy()
+        assert abs(got - ref) <= TOL[precision] * scale, (precision, got, ref, scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gradient_262144_subset(precision):
+    """The 262,144-particle mixture: dE/dr of a 512-particle subset against the
+    oracle's analytic gradient, and against central differences (h = 1e-4) of
+    the particle's energy evaluated on the GPU, skipping coordinates with a
+    partner within 2h of the cutoff (the truncated energy jumps there)."""
+    w = W.c5_gradient()
+    types = w.types()
+    pos = w.positions()
+    o = O.System(w.L, w.rc, w.eps, w.sigma)
+    o.build(pos, types)
+    ref = o.energy_grad()
+    b = Box(w.L, w.rc, w.eps, w.sigma, precision=precision)
+    b.build_cells(torch.as_tensor(pos), torch.as_tensor(types))
+    g = b.energy_grad()
+    dpos = g["dpos"].cpu().numpy().astype(np.float64)
+    rows = np.random.default_rng(512).choice(len(pos), 512, replace=False)
+    sm = species_major_order(types)
+    # analytic: species-major rows of the GPU result against the oracle's
+    fs = np.abs(ref["dpos"][rows]).max()
+    tol = 1e-5 if precision == "fp32" else 1e-9
+    assert np.allclose(dpos[rows], ref["dpos"][rows], rtol=tol, atol=tol * fs)
+    for k in ("deps", "dsigma"):
+        assert np.allclose(g[k], ref[k], rtol=10 * TOL[precision])
+    # central differences of the particle's energy (exclude itself) on the GPU
+    n_o, X, _, _ = o.state()
+    cnt = o.counts()
+    base = np.concatenate([[0], np.cumsum(cnt)])
+    h = 1e-4
+    q = 2.0 ** 32 / w.L
+    pts, sps, exc, meta = [], [], [], []
+    for r in rows:
+        s = int(np.searchsorted(base, r, side="right") - 1)
+        i = r - base[s]
+        P = X[r].astype(np.float64) / q
+        for ax in range(3):
+            for sgn in (1.0, -1.0):
+                p = P.copy()
+                p[ax] = (p[ax] + sgn * h) % w.L
+                pts.append(p)
+                sps.append(s)
+                exc.append((s << 32) | i)
+            meta.append((r, ax))
+    pts = np.array(pts)
+    e = b.trial_energy(pts, np.array(sps, np.int32), exclude=np.array(exc, np.int64)).cpu().numpy()
+    # the grid positions the points quantise to (the step actually taken)
+    Xq = np.floor(pts * q).astype(np.int64) % (1 << 32)
+    checked = 0
+    for j, (r, ax) in enumerate(meta):
+        xp, xm = Xq[2 * j, ax], Xq[2 * j + 1, ax]
+        step = ((xp - xm + (1 << 31)) % (1 << 32) - (1 << 31)) / q
+        if _near_cutoff(X, r, w.L, w.rc, 2 * h):
+            continue
+        fd = (e[2 * j] - e[2 * j + 1]) / step
+        scale = max(abs(ref["dpos"][r, ax]), 1.0)
+        assert abs(fd - dpos[r, ax]) <= 2e-3 * scale, (r, ax, fd, dpos[r, ax])
+        checked += 1
+    assert checked > 1000
+    del sm, n_o
+
+
+def _near_cutoff(X, r, L, rc, band):
+    """Whether particle r (grid coordinates X, species-major rows) has a
+    partner whose distance lies within `band` of rc."""
+    q = 2.0 ** 32 / L
+    d = (X.astype(np.int64) - X[r].astype(np.int64) + (1 << 31)) % (1 << 32) - (1 << 31)
+    dist = np.sqrt(((d / q) ** 2).sum(1))
+    return bool(np.any(np.abs(dist - rc) <= band))

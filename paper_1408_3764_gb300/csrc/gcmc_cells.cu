@@ -119,8 +119,7 @@ __global__ void k_scan_apply(const int32_t *__restrict__ in, int64_t n, const in
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[nb];
 }
 
-static gcmc_status exclusive_scan(gcmc_ctx *ctx, const int32_t *in, int64_t n, int32_t *out,
-                                  int32_t *part, int *vmax)
+gcmc_status exclusive_scan(gcmc_ctx *ctx, const int32_t *in, int64_t n, int32_t *out, int32_t *part, int *vmax)
 {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) {

@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "gcmc_ctx.h"
+#include "gcmc_stage.cuh"
 
 namespace gcmc {
 
@@ -101,55 +102,7 @@ constexpr int kRW = 128;      // words ring
 constexpr int kFill = 32;     // words filled per keeper round
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a wait gives up after 1 s (default)
 
-// A bounded wait: expired() turns true once the wait has lasted `limit` ns
-// (global timer, read every 256 polls).
-struct Wait {
-    unsigned long long t0 = 0;
-    unsigned polls = 0;
-    __device__ __forceinline__ bool expired(unsigned long long limit)
-    {
-        if ((++polls & 255u) != 0u) return false;
-        unsigned long long now;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-        if (t0 == 0) t0 = now;
-        return now - t0 > limit;
-    }
-};
 constexpr uint32_t kOld = 1u, kNew = 2u;
-
-// ---------------------------------------------------------------- float-float
-struct FF {
-    float hi, lo;
-};
-__device__ __forceinline__ FF ff_add(FF a, FF b)
-{
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb);
-    const float t = e + a.lo + b.lo;
-    const float h = s + t;
-    return FF{h, t - (h - s)};
-}
-__device__ __forceinline__ FF ff_add_f(FF a, float x)
-{
-    const float s = a.hi + x;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (x - bb);
-    const float t = e + a.lo;
-    const float h = s + t;
-    return FF{h, t - (h - s)};
-}
-__device__ __forceinline__ FF ff_warp_sum(FF v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        FF w;
-        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-        v = ff_add(v, w);
-    }
-    return v;
-}
 
 // ---------------------------------------------------------------- trials
 struct Trial {

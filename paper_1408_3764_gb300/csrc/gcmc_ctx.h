@@ -102,6 +102,9 @@ gcmc_status read_status(gcmc_ctx *ctx, int *bits);
 gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
 gcmc_status make_compact(gcmc_ctx *ctx);
 gcmc_status relayout(gcmc_ctx *ctx, int new_cap, int64_t new_maxN);
+// out[i] = exclusive prefix sum of in[0 .. n), out[n] = the total; part:
+// (n + 1023) / 1024 + 1 ints of scratch, vmax: one int (the largest value).
+gcmc_status exclusive_scan(gcmc_ctx *ctx, const int32_t *in, int64_t n, int32_t *out, int32_t *part, int *vmax);
 
 // energy.cu
 gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species,

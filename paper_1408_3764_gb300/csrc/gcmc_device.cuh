@@ -225,6 +225,40 @@ __device__ __forceinline__ void lj_f64(const GridSep &s, double c4e, double sig2
     }
 }
 
+// Float-float values (hi + lo) and their sums (TwoSum on the high words).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float t = e + a.lo + b.lo;
+    const float h = s + t;
+    return FF{h, t - (h - s)};
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float x)
+{
+    const float s = a.hi + x;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (x - bb);
+    const float t = e + a.lo;
+    const float h = s + t;
+    return FF{h, t - (h - s)};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------

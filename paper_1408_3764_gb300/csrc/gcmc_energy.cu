@@ -1,17 +1,24 @@
 // gcmc_energy.cu -- cell-list energies on the compact cell-major layout:
 //   k_trial_energy   energy of many trial points against their 27 cells
-//                    (Algorithms 6 and 7, one warp per trial point);
+//                    (Algorithms 6 and 7); the points are binned by cell and
+//                    one CTA evaluates all points of a cell against its
+//                    neighbourhood, staged once into shared memory;
 //   k_cell_energy    full-system energy and virial, one CTA per home cell
-//                    (the cell-list CalculateTotalEnergy of Sec. 3.1.1);
+//                    over its half shell (the cell-list CalculateTotalEnergy
+//                    of Sec. 3.1.1);
 //   k_cell_grad      its hand-written gradient (positions, eps, sigma, virial).
-// FP32 mode: pair terms and per-lane sums in FP32, sums across cells in
-// FP64.  FP64 mode: everything in FP64.
+// FP32 mode: an FP32 screen of every candidate, compensated FP32 pair terms
+// and sums for the energies (float-float, lj_ff), FP32 pair terms for the
+// gradient with compensated scalar sums; sums across cells in FP64.
+// FP64 mode: everything in FP64.  k_cell_energy_padded (allocation-free
+// energy) keeps plain FP32 pair terms and per-lane sums in FP32 mode.
 #include <cmath>
 #include <mutex>
 #include <string>
 #include <type_traits>
 
 #include "gcmc_ctx.h"
+#include "gcmc_stage.cuh"
 
 namespace gcmc {
 
@@ -45,56 +52,6 @@ struct Acc<false> {
     __device__ __forceinline__ double av() const { return a; }
 };
 
-// Up to 18 contiguous runs of the compact layout cover the 27 cells around
-// cell (cx, cy, cz): per (dy, dz) row the three x-neighbours are one run, or
-// two when the row wraps around the box.
-struct Runs {
-    int start[18];
-    int end[18];  // inclusive prefix of lengths (flat index space)
-};
-
-__device__ __forceinline__ void row_runs(const int32_t *__restrict__ cs, int T, int cx, int cy, int cz,
-                                         int r, int part, int &b, int &len)
-{
-    int dy = r % 3 - 1, dz = r / 3 - 1;
-    int ny = cy + dy, nz = cz + dz;
-    ny += (ny < 0) ? T : 0;
-    ny -= (ny >= T) ? T : 0;
-    nz += (nz < 0) ? T : 0;
-    nz -= (nz >= T) ? T : 0;
-    const int row = (nz * T + ny) * T;
-    int lo, hi;  // cell range [lo, hi) within the row
-    if (cx >= 1 && cx <= T - 2) {
-        lo = part == 0 ? cx - 1 : 0;
-        hi = part == 0 ? cx + 2 : 0;
-    } else if (cx == 0) {
-        lo = part == 0 ? 0 : T - 1;
-        hi = part == 0 ? 2 : T;
-    } else {
-        lo = part == 0 ? T - 2 : 0;
-        hi = part == 0 ? T : 1;
-    }
-    b = cs[row + lo];
-    len = cs[row + hi] - b;
-    if (hi == lo) len = 0;
-}
-
-// Builds the run table of one warp in shared memory; returns the item count.
-__device__ __forceinline__ int warp_runs(const int32_t *__restrict__ cs, int T, int cx, int cy, int cz,
-                                         Runs &R)
-{
-    const int lane = threadIdx.x & 31;
-    int b = 0, len = 0;
-    if (lane < 18) row_runs(cs, T, cx, cy, cz, lane % 9, lane / 9, b, len);
-    const int inc = warp_inclusive_scan(len);
-    if (lane < 18) {
-        R.start[lane] = b;
-        R.end[lane] = inc;
-    }
-    __syncwarp();
-    return __shfl_sync(0xffffffffu, inc, 17);
-}
-
 template <bool F32>
 __device__ __forceinline__ void pair_acc(const uint4 &p, const uint4 &q, uint32_t excl, uint64_t R2,
                                          int t, const FieldF &ff, const FieldD &fd, Acc<F32> &acc)
@@ -124,145 +81,418 @@ __device__ __forceinline__ uint32_t quantize_dev(double x, double q, bool &ok)
     return (uint32_t)(unsigned long long)(long long)floor(t);
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(256) k_trial_energy(
-    const double *__restrict__ pos, const int32_t *__restrict__ species, const int64_t *__restrict__ exclude,
-    int64_t m, const uint4 *__restrict__ cpos, const int32_t *__restrict__ cs, int T, double q, uint64_t R2,
-    int S, const FieldF ff, const FieldD fd, double *__restrict__ out, double *__restrict__ out_abs,
-    int *__restrict__ status)
+// ---------------------------------------------------------------------------
+// Neighbourhood kernels.  One CTA per cell: the cell's neighbourhood (the 27
+// cells, or the home cell and its half shell) is staged into shared memory
+// by bulk copies (gcmc_stage.cuh), at most kBuf records per pass, and each
+// staged record is converted once to float coordinates relative to the home
+// cell's centre.  Warps take the cell's points (trial points or home
+// particles), lanes the staged records: the FP32 squared distance screens the
+// cutoff (the exact integer squared distance decides inside a thin band
+// around rc^2), the pairs inside the cutoff join the warp's queue and are
+// evaluated 32 at a time -- in compensated FP32 (lj_ff) in FP32 mode, in FP64
+// in FP64 mode -- so the long pair term runs only on the ~15 % of
+// candidates inside the cutoff, with every lane busy.
+//
+// Minimum image relative to the cell centre c: a partner within rc of a
+// point p of the cell lies, along each axis, within rc + S/2 of c.  When
+// S >= rc (T = floor(L / rc) >= 3) that is at most 1.5 S <= L / 2, so the
+// wrapped difference q - c already gives the image nearest to p.  A box
+// with 2 rc <= L < 3 rc has T = 3 and S < rc: there the FP32 separation is
+// wrapped once more into [-L/2, L/2] (wrap = 1).  The queued pairs use the
+// exact wrapped integer difference p - q.
+// ---------------------------------------------------------------------------
+constexpr int kBuf = 1024;    // staged records per pass
+constexpr int kPChunk = 64;   // points per chunk (per-point sums in shared memory)
+constexpr int kNbWarps = 8;   // warps of a neighbourhood CTA
+constexpr int kNbQ = 64;      // queue entries per warp (a ring)
+
+// Grid coordinate of the centre of cell k along an axis of T cells.
+__device__ __forceinline__ uint32_t cell_centre(int k, int T)
 {
-    __shared__ Runs runs[8];
+    return (uint32_t)((((unsigned long long)(2 * k + 1)) << 32) / (unsigned long long)(2 * T));
+}
+
+__device__ __forceinline__ float rel_f(uint32_t a, uint32_t c) { return (float)(int)(a - c); }
+
+// Shared state of a neighbourhood CTA.
+struct __align__(16) NbShared {
+    uint4 raw[kBuf];     // staged records (X, Y, Z, tag)
+    float4 fl[kBuf];     // the same relative to the home cell centre, tag bits in .w
+    int q[kNbWarps][kNbQ];
+    RunList runs;
+    uint64_t bar;
+    int nbad;
+};
+
+// The per-warp queue of staged indices of pairs inside the cutoff.
+struct NbQueue {
+    int *buf;
+    int head, n;
+};
+
+template <typename Drain>
+__device__ __forceinline__ void nb_push(NbQueue &Q, bool in, int f, Drain &D)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned bm = __ballot_sync(0xffffffffu, in);
+    if (bm == 0u) return;
+    if (in) Q.buf[(Q.head + Q.n + __popc(bm & ((1u << lane) - 1u))) & (kNbQ - 1)] = f;
+    Q.n += __popc(bm);
+    if (Q.n >= 32) {
+        __syncwarp();
+        D(Q.buf[(Q.head + lane) & (kNbQ - 1)], true);
+        Q.head = (Q.head + 32) & (kNbQ - 1);
+        Q.n -= 32;
+        __syncwarp();
+    }
+}
+
+template <typename Drain>
+__device__ __forceinline__ void nb_flush(NbQueue &Q, Drain &D)
+{
+    const int lane = threadIdx.x & 31;
+    if (Q.n > 0) {
+        __syncwarp();
+        const bool have = lane < Q.n;
+        D(have ? Q.buf[(Q.head + lane) & (kNbQ - 1)] : 0, have);
+        Q.head = (Q.head + Q.n) & (kNbQ - 1);
+        Q.n = 0;
+    }
+    __syncwarp();
+}
+
+// Screens the staged records [f0, nst) against point P (float position pf
+// relative to the centre) and queues those inside the cutoff.  skip(f)
+// leaves a record out (the point itself, or home-cell pairs met from the
+// other side).
+__device__ __forceinline__ float wrap_grid(float d)
+{
+    return fmaf(-4294967296.0f, rintf(d * 2.3283064365386963e-10f), d);  // d - 2^32 rint(d / 2^32)
+}
+
+template <typename Skip, typename Drain>
+__device__ __forceinline__ void nb_screen(const NbShared &sh, int nst, const uint4 &P, const float3 &pf, uint64_t R2,
+                                          float r2lo, float r2hi, bool wrap, NbQueue &Q, Skip skip, Drain &D)
+{
+    const int lane = threadIdx.x & 31;
+    for (int b = 0; b < nst; b += 32) {
+        const int f = b + lane;
+        bool in = false, band = false;
+        if (f < nst) {
+            const float4 q = sh.fl[f];
+            if (!skip(f, __float_as_uint(q.w))) {
+                float dx = pf.x - q.x, dy = pf.y - q.y, dz = pf.z - q.z;
+                if (wrap) {
+                    dx = wrap_grid(dx);
+                    dy = wrap_grid(dy);
+                    dz = wrap_grid(dz);
+                }
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                in = r2 < r2lo;
+                band = r2 >= r2lo && r2 <= r2hi;
+            }
+        }
+        if (__any_sync(0xffffffffu, band)) {
+            if (band) {
+                const GridSep s = grid_sep(P, sh.raw[f]);
+                in = s.g < R2;
+            }
+        }
+        nb_push(Q, in, f, D);
+    }
+}
+
+// Stages the items [w0, w1) of the neighbourhood into the shared buffers
+// (bulk copies, then the float conversion).  Returns false -- in every
+// thread -- when the copy did not land within the wait limit; the timeout
+// bit is then set and the block must return.
+__device__ __forceinline__ bool nb_stage(NbShared &sh, const uint4 *__restrict__ cpos, int w0, int w1,
+                                         uint32_t cx0, uint32_t cy0, uint32_t cz0, unsigned &parity,
+                                         int *__restrict__ status)
+{
+    __syncthreads();  // the previous pass's readers are done with the buffers
+    if (w1 <= w0) return true;
+    if (threadIdx.x == 0) stage_issue(cpos, sh.runs, w0, w1, sh.raw, &sh.bar);
+    const bool ok = stage_wait(&sh.bar, parity, 1000000000ull);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(status, kStatusTimeout);
+            stage_wait(&sh.bar, parity, 1000000000ull);  // the copies in flight land before the block ends
+        }
+        __syncthreads();
+        return false;
+    }
+    parity ^= 1u;
+    for (int f = threadIdx.x; f < w1 - w0; f += blockDim.x) {
+        const uint4 r = sh.raw[f];
+        sh.fl[f] = make_float4(rel_f(r.x, cx0), rel_f(r.y, cy0), rel_f(r.z, cz0), __uint_as_float(r.w));
+    }
+    __syncthreads();
+    return true;
+}
+
+// ---- trial energies ---------------------------------------------------
+// Per trial point: species, the excluded particle's tag, the grid position.
+struct TrialPt {
+    uint4 P;       // grid X, Y, Z; .w = species
+    uint32_t excl; // tag of the excluded particle, or ~0
+    int idx;       // the point's input index
+};
+
+template <bool F32>
+struct TrialDrain {
+    const NbShared &sh;
+    uint4 P;
+    int t;
+    const FieldF &ff;
+    const FieldD &fd;
+    float eh = 0.f, el = 0.f, mag = 0.f;
+    double de = 0.0, da = 0.0;
+    __device__ TrialDrain(const NbShared &s, const uint4 &p, int t_, const FieldF &f, const FieldD &d)
+        : sh(s), P(p), t(t_), ff(f), fd(d)
+    {
+    }
+    __device__ __forceinline__ void operator()(int f, bool have)
+    {
+        if (!have) return;
+        const uint4 r = sh.raw[f];
+        const int k = t * kMaxSpecies + (int)tag_species(r.w);
+        const int ex = (int)(P.x - r.x), ey = (int)(P.y - r.y), ez = (int)(P.z - r.z);
+        if constexpr (F32) {
+            float uh, ul, m;
+            lj_ff(ex, ey, ez, ff.c4e[k], ff.c4e_lo[k], ff.sig2[k], ff.sig2_lo[k], uh, ul, m);
+            ff_acc(eh, el, uh, ul);
+            mag += m;
+        } else {
+            GridSep s;
+            s.dx = ex;
+            s.dy = ey;
+            s.dz = ez;
+            s.g = (unsigned long long)((long long)ex * ex) + (unsigned long long)((long long)ey * ey) +
+                  (unsigned long long)((long long)ez * ez);
+            double u, m;
+            lj_f64(s, fd.c4e[k], fd.sig2[k], u, m);
+            de += u;
+            da += m;
+        }
+    }
+};
+
+// Trial points binned by cell: cell c holds the points pts[ps[c] .. ps[c+1]).
+template <bool F32>
+__global__ void __launch_bounds__(kNbWarps * 32) k_trial_energy(
+    const TrialPt *__restrict__ pts, const int32_t *__restrict__ ps, const uint4 *__restrict__ cpos,
+    const int32_t *__restrict__ cs, int T, int64_t ncell, uint64_t R2, float r2lo, float r2hi, bool wrap,
+    const __grid_constant__ FieldF ff, const __grid_constant__ FieldD fd, double *__restrict__ out,
+    double *__restrict__ out_abs, int *__restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
+    __shared__ double2 part[kPChunk];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Runs &R = runs[w];
-    const int64_t warps = (int64_t)gridDim.x * 8;
-    for (int64_t k = (int64_t)blockIdx.x * 8 + w; k < m; k += warps) {
-        // lanes 0, 1, 2 quantise x, y, z (FP64 work on three lanes only)
-        bool ok = true;
-        uint32_t Xl = 0u;
-        if (lane < 3) Xl = quantize_dev(pos[3 * k + lane], q, ok);
-        ok = __all_sync(0xffffffffu, ok);
-        uint4 P;
-        P.x = __shfl_sync(0xffffffffu, Xl, 0);
-        P.y = __shfl_sync(0xffffffffu, Xl, 1);
-        P.z = __shfl_sync(0xffffffffu, Xl, 2);
-        const int t = species[k];
+    if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    NbQueue Q = {sh.q[w], 0, 0};
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int p0 = ps[c], p1 = ps[c + 1];
+        if (p1 == p0) continue;  // uniform across the block
+        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
+        __syncthreads();
+        if (w == 0) runs27(cs, T, cx, cy, cz, sh.runs);
+        __syncthreads();
+        const int total = sh.runs.end[17];
+        const uint32_t cx0 = cell_centre(cx, T), cy0 = cell_centre(cy, T), cz0 = cell_centre(cz, T);
+        for (int pb = p0; pb < p1; pb += kPChunk) {
+            const int pn = min(kPChunk, p1 - pb);
+            __syncthreads();  // the previous chunk's sums have been written out
+            for (int i = threadIdx.x; i < pn; i += blockDim.x) part[i] = make_double2(0.0, 0.0);
+            for (int base = 0; base < max(total, 1); base += kBuf) {
+                const int nst = min(kBuf, total - base);
+                if (!nb_stage(sh, cpos, base, base + max(nst, 0), cx0, cy0, cz0, parity, status)) return;
+                for (int i = w; i < pn; i += kNbWarps) {
+                    const TrialPt tp = pts[pb + i];
+                    const float3 pf = make_float3(rel_f(tp.P.x, cx0), rel_f(tp.P.y, cy0), rel_f(tp.P.z, cz0));
+                    TrialDrain<F32> D(sh, tp.P, (int)tp.P.w, ff, fd);
+                    const uint32_t ex = tp.excl;
+                    nb_screen(sh, max(nst, 0), tp.P, pf, R2, r2lo, r2hi, wrap, Q,
+                              [&](int, uint32_t tag) { return tag == ex; }, D);
+                    nb_flush(Q, D);
+                    double e, a;
+                    if constexpr (F32) {
+                        const FF s = ff_warp_sum(FF{D.eh, D.el});
+                        e = (double)s.hi + (double)s.lo;
+                        a = (double)warp_sum(D.mag);
+                    } else {
+                        e = warp_sum(D.de);
+                        a = warp_sum(D.da);
+                    }
+                    if (lane == 0) {
+                        part[i].x += e;
+                        part[i].y += a;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+                const int k = pts[pb + i].idx;
+                out[k] = part[i].x;
+                if (out_abs) out_abs[k] = part[i].y;
+            }
+        }
+    }
+}
+
+// Quantises the trial points, bins them by cell (count per cell) and keeps
+// their exclusion tags; bad input gets NaN at once and no cell.
+__global__ void k_trial_bin(const double *__restrict__ pos, const int32_t *__restrict__ species,
+                            const int64_t *__restrict__ exclude, int64_t m, double q, int T, int S,
+                            TrialPt *__restrict__ tmp, int32_t *__restrict__ cellid, int32_t *__restrict__ count,
+                            double *__restrict__ out, double *__restrict__ out_abs, int *__restrict__ status)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int s = species[k];
+        bool ok = s >= 0 && s < S;
+        uint32_t X[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) X[a] = quantize_dev(pos[3 * k + a], q, ok);
+        if (!ok) {
+            atomicOr(status, kStatusBadInput);
+            out[k] = __longlong_as_double(0x7ff8000000000000ll);
+            if (out_abs) out_abs[k] = out[k];
+            cellid[k] = -1;
+            continue;
+        }
         uint32_t excl = 0xFFFFFFFFu;
         if (exclude) {
             const int64_t x = exclude[k];
             if (x >= 0) excl = make_tag((uint32_t)(x & 0xFFFFFFFFll), (uint32_t)(x >> 32));
         }
-        if (!ok || t < 0 || t >= S) {
-            if (lane == 0) {
-                out[k] = __longlong_as_double(0x7ff8000000000000ll);
-                if (out_abs) out_abs[k] = out[k];
-                atomicOr(status, kStatusBadInput);
-            }
-            continue;
-        }
-        const int cx = cell_coord(P.x, T), cy = cell_coord(P.y, T), cz = cell_coord(P.z, T);
-        const int total = warp_runs(cs, T, cx, cy, cz, R);
-        Acc<F32> acc;
-        int r = 0;
-        for (int f = lane; f < total; f += 32) {
-            while (f >= R.end[r]) ++r;
-            const int idx = R.start[r] + f - (r ? R.end[r - 1] : 0);
-            const uint4 qv = cpos[idx];
-            pair_acc<F32>(P, qv, excl, R2, t, ff, fd, acc);
-        }
-        double e, a;
-        if constexpr (F32) {
-            e = (double)warp_sum(acc.e);
-            a = (double)warp_sum(acc.a);
-        } else {
-            e = warp_sum(acc.ev());
-            a = warp_sum(acc.av());
-        }
-        if (lane == 0) {
-            out[k] = e;
-            if (out_abs) out_abs[k] = a;
-        }
-        __syncwarp();
+        const int c = cell_of(X[0], X[1], X[2], T);
+        TrialPt tp;
+        tp.P = make_uint4(X[0], X[1], X[2], (uint32_t)s);
+        tp.excl = excl;
+        tp.idx = (int)k;
+        tmp[k] = tp;
+        cellid[k] = c;
+        atomicAdd(&count[c], 1);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Full-system energy: one CTA per home cell.  Each unordered pair is visited
-// once: the home cell against itself (j after i) and against the 13 cells of
-// a half shell of its neighbours (offsets after (0,0,0) in z, y, x order);
-// the other 13 neighbours see this cell from their own half shells.  The 14
-// cells are staged in shared memory, warps take home particles, lanes take
-// the staged partners.
-// ---------------------------------------------------------------------------
-constexpr int kStage = 2048;  // staged partners per pass (32 KB)
-
-template <bool F32>
-__global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ cpos,
-                                                     const int32_t *__restrict__ cs, int T, int64_t ncell,
-                                                     uint64_t R2, const FieldF ff, const FieldD fd,
-                                                     double *__restrict__ partial)
+// Scatters the binned points into their cells' ranges (order within a cell
+// does not matter: each point's sum is computed by one warp on its own).
+__global__ void k_trial_place(const TrialPt *__restrict__ tmp, const int32_t *__restrict__ cellid, int64_t m,
+                              const int32_t *__restrict__ ps, int32_t *__restrict__ fill, TrialPt *__restrict__ pts)
 {
-    __shared__ uint4 stage[kStage];
-    __shared__ int rs[14], re[14];  // start of each staged cell, inclusive end of its items
-    __shared__ double red[8][2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
-        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
-        if (w == 0) {
-            // lane 0: the home cell; lanes 1 .. 13: offsets 14 .. 26 of the
-            // 3 x 3 x 3 block in (z, y, x) order, i.e. those after (0, 0, 0)
-            int len = 0, st = 0;
-            if (lane < 14) {
-                const int k = lane == 0 ? 13 : 13 + lane;
-                const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-                int x = cx + dx, y = cy + dy, z = cz + dz;
-                x += (x < 0) ? T : 0;
-                x -= (x >= T) ? T : 0;
-                y += (y < 0) ? T : 0;
-                y -= (y >= T) ? T : 0;
-                z += (z < 0) ? T : 0;
-                z -= (z >= T) ? T : 0;
-                const int cell = (z * T + y) * T + x;
-                st = cs[cell];
-                len = cs[cell + 1] - st;
-            }
-            const int inc = warp_inclusive_scan(len);
-            if (lane < 14) {
-                rs[lane] = st;
-                re[lane] = inc;
-            }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cellid[k];
+        if (c < 0) continue;
+        pts[ps[c] + atomicAdd(&fill[c], 1)] = tmp[k];
+    }
+}
+
+// ---- full-system energy ---------------------------------------------------
+template <bool F32>
+struct PairDrain {
+    const NbShared &sh;
+    uint4 P;
+    int t;
+    const FieldF &ff;
+    const FieldD &fd;
+    float eh = 0.f, el = 0.f, wh = 0.f, wl = 0.f;
+    double de = 0.0, dw = 0.0;
+    __device__ PairDrain(const NbShared &s, const FieldF &f, const FieldD &d) : sh(s), ff(f), fd(d) {}
+    __device__ __forceinline__ void operator()(int f, bool have)
+    {
+        if (!have) return;
+        const uint4 r = sh.raw[f];
+        const int k = t * kMaxSpecies + (int)tag_species(r.w);
+        const int ex = (int)(P.x - r.x), ey = (int)(P.y - r.y), ez = (int)(P.z - r.z);
+        if constexpr (F32) {
+            float uh, ul, m;
+            lj_ff(ex, ey, ez, ff.c4e[k], ff.c4e_lo[k], ff.sig2[k], ff.sig2_lo[k], uh, ul, m);
+            ff_acc(eh, el, uh, ul);
+            ff_acc(wh, wl, -fmaf(3.f, m, 9.f * uh), 0.f);  // r U'(r) = -12 rep + 6 att
+        } else {
+            GridSep s;
+            s.dx = ex;
+            s.dy = ey;
+            s.dz = ez;
+            s.g = (unsigned long long)((long long)ex * ex) + (unsigned long long)((long long)ey * ey) +
+                  (unsigned long long)((long long)ez * ez);
+            double u, m;
+            lj_f64(s, fd.c4e[k], fd.sig2[k], u, m);
+            de += u;
+            dw -= 3.0 * m + 9.0 * u;
         }
-        __syncthreads();
-        const int total = re[13];
-        const int h0 = cs[c], h1 = cs[c + 1];
-        Acc<F32> acc;
-        for (int base = 0; base < total; base += kStage) {
-            const int nst = min(kStage, total - base);
-            for (int f = threadIdx.x; f < nst; f += blockDim.x) {
-                const int g = base + f;
-                int r = 0;
-                while (g >= re[r]) ++r;
-                stage[f] = cpos[rs[r] + g - (r ? re[r - 1] : 0)];
-            }
+    }
+};
+
+// One CTA per home cell; each unordered pair once: the home cell against
+// itself (partners after the particle) and against the 13 cells of its half
+// shell; the other 13 neighbours see the cell from their own half shells.
+// partial[2c], partial[2c+1] = the cell's energy and virial sums.
+template <bool F32>
+__global__ void __launch_bounds__(kNbWarps * 32) k_cell_energy(const uint4 *__restrict__ cpos,
+                                                               const int32_t *__restrict__ cs, int T, int64_t ncell,
+                                                               uint64_t R2, float r2lo, float r2hi, bool wrap,
+                                                               const __grid_constant__ FieldF ff,
+                                                               const __grid_constant__ FieldD fd,
+                                                               double *__restrict__ partial, int *__restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
+    __shared__ double red[kNbWarps][2];
+    __shared__ uint4 home[kPChunk];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    NbQueue Q = {sh.q[w], 0, 0};
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int h0 = cs[c], nh = cs[c + 1] - h0;
+        PairDrain<F32> D(sh, ff, fd);
+        if (nh > 0) {
+            const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
             __syncthreads();
-            for (int i = h0 + w; i < h1; i += 8) {
-                const uint4 p = cpos[i];
-                const int t = (int)tag_species(p.w);
-                const int hi = i - h0;  // the home cell's items come first
-                for (int f = lane; f < nst; f += 32) {
-                    const int g = base + f;
-                    if (g <= hi) continue;  // within the home cell: partners after i only
-                    pair_acc<F32>(p, stage[f], 0xFFFFFFFFu, R2, t, ff, fd, acc);
+            if (w == 0) runs_half(cs, T, cx, cy, cz, sh.runs);
+            __syncthreads();
+            const int total = sh.runs.end[9];
+            const uint32_t cx0 = cell_centre(cx, T), cy0 = cell_centre(cy, T), cz0 = cell_centre(cz, T);
+            for (int pb = 0; pb < nh; pb += kPChunk) {
+                const int pn = min(kPChunk, nh - pb);
+                __syncthreads();
+                for (int i = threadIdx.x; i < pn; i += blockDim.x) home[i] = cpos[h0 + pb + i];
+                for (int base = 0; base < total; base += kBuf) {
+                    const int nst = min(kBuf, total - base);
+                    if (!nb_stage(sh, cpos, base, base + nst, cx0, cy0, cz0, parity, status)) return;
+                    for (int i = w; i < pn; i += kNbWarps) {
+                        const int hi = pb + i;  // the particle's item index (home items come first)
+                        D.P = home[i];
+                        D.t = (int)tag_species(D.P.w);
+                        const float3 pf =
+                            make_float3(rel_f(D.P.x, cx0), rel_f(D.P.y, cy0), rel_f(D.P.z, cz0));
+                        nb_screen(sh, nst, D.P, pf, R2, r2lo, r2hi, wrap, Q,
+                                  [&](int f, uint32_t) {
+                                      const int g = base + f;
+                                      return g < nh && g <= hi;
+                                  },
+                                  D);
+                        nb_flush(Q, D);
+                    }
                 }
             }
-            __syncthreads();
         }
         double e, vw;
         if constexpr (F32) {
-            e = (double)warp_sum(acc.e);
-            vw = (double)warp_sum(acc.w);
+            const FF s = ff_warp_sum(FF{D.eh, D.el});
+            const FF v = ff_warp_sum(FF{D.wh, D.wl});
+            e = (double)s.hi + (double)s.lo;
+            vw = (double)v.hi + (double)v.lo;
         } else {
-            e = warp_sum(acc.ev());
-            vw = warp_sum(acc.w);
+            e = warp_sum(D.de);
+            vw = warp_sum(D.dw);
         }
         if (lane == 0) {
             red[w][0] = e;
@@ -271,8 +501,8 @@ __global__ void __launch_bounds__(256) k_cell_energy(const uint4 *__restrict__ c
         __syncthreads();
         if (threadIdx.x < 2) {
             double sum = 0.0;
-            for (int k = 0; k < 8; ++k) sum += red[k][threadIdx.x];
-            partial[2 * c + threadIdx.x] = sum;  // energy, virial
+            for (int k = 0; k < kNbWarps; ++k) sum += red[k][threadIdx.x];
+            partial[2 * c + threadIdx.x] = sum;
         }
         __syncthreads();
     }
@@ -304,103 +534,180 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int64_t n, in
 //   r U'(r) = -12 rep + 6 att,
 //   dE/deps_ab (half of each ordered pair) += 2 (s^12 - s^6),
 //   dE/dsigma_ab (same) += (12 rep - 6 att) / (2 sigma_ab).
-// One warp per home particle; the per-cell scalars go to `partial` rows of
-// width 2 + 2 S^2: [E, virial, deps..., dsigma...].  NS: partner species
-// kept in registers (the species count when it is 1 or 2, else kMaxSpecies).
-// FP32 mode sums per lane and across the warp in FP32, per CTA in FP64.
+// One CTA per home cell with its 27 cells staged; one warp per home
+// particle; every pair is met from both of its particles (the forces of a
+// particle are summed by one warp, so nothing is scattered).  The per-cell
+// scalars go to `partial` rows of width 2 + 2 S^2: [E, virial, deps...,
+// dsigma...].  NS: partner species in registers (1, 2, or kMaxSpecies).
+// FP32 mode: FP32 pair terms from the exact integer r^2, forces summed in
+// FP32 per lane and FP64 across the warp, the scalars summed in
+// compensated FP32; FP64 mode: FP64 throughout.
 // ---------------------------------------------------------------------------
 template <bool F32, int NS>
-__global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpos, const int32_t *__restrict__ cs,
-                                                   int T, int64_t ncell, uint64_t R2, int S, const FieldF ff,
-                                                   const FieldD fd, double inv_h, const int64_t *__restrict__ d_n,
-                                                   float *__restrict__ dpos, double *__restrict__ partial)
-{
+struct GradDrain {
     using R = typename std::conditional<F32, float, double>::type;
+    const NbShared &sh;
+    uint4 P;
+    int t;
+    const FieldF &ff;
+    const FieldD &fd;
+    R fx = 0, fy = 0, fz = 0;
+    float eh = 0.f, el = 0.f, wh = 0.f, wl = 0.f;  // FP32 mode
+    double de = 0.0, dw = 0.0;                    // FP64 mode
+    R aEps[NS], aSig[NS];
+    __device__ GradDrain(const NbShared &s, const FieldF &f, const FieldD &d) : sh(s), ff(f), fd(d)
+    {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) aEps[q] = aSig[q] = 0;
+    }
+    __device__ __forceinline__ void operator()(int f, bool have)
+    {
+        if (!have) return;
+        const uint4 r = sh.raw[f];
+        const int ts = (int)tag_species(r.w);
+        const int k = t * kMaxSpecies + ts;
+        const int ex = (int)(P.x - r.x), ey = (int)(P.y - r.y), ez = (int)(P.z - r.z);
+        const unsigned long long g = (unsigned long long)((long long)ex * ex) +
+                                     (unsigned long long)((long long)ey * ey) +
+                                     (unsigned long long)((long long)ez * ez);
+        R r2, c4e, sig2;
+        if constexpr (F32) {
+            r2 = __ull2float_rn(g);
+            c4e = ff.c4e[k];
+            sig2 = ff.sig2[k];
+        } else {
+            r2 = (double)g;
+            c4e = fd.c4e[k];
+            sig2 = fd.sig2[k];
+        }
+        const R s2 = sig2 / r2;
+        const R s6 = s2 * s2 * s2;
+        const R rep = c4e * s6 * s6, att = c4e * s6;
+        const R rdu = (R)(-12) * rep + (R)6 * att;  // r U'(r)
+        const R coef = rdu / r2;
+        fx += coef * (R)ex;
+        fy += coef * (R)ey;
+        fz += coef * (R)ez;
+        if constexpr (F32) {
+            ff_acc(eh, el, 0.5f * (rep - att), 0.f);
+            ff_acc(wh, wl, 0.5f * rdu, 0.f);
+        } else {
+            de += 0.5 * (rep - att);
+            dw += 0.5 * rdu;
+        }
+        const R ge = (R)2 * (s6 * s6 - s6);
+        const R gs = (R)0.5 * ((R)12 * rep - (R)6 * att);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            if (q == ts) {
+                aEps[q] += ge;
+                aSig[q] += gs;
+            }
+        }
+    }
+};
+
+template <bool F32, int NS>
+__global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__restrict__ cpos,
+                                                             const int32_t *__restrict__ cs, int T, int64_t ncell,
+                                                             uint64_t R2, float r2lo, float r2hi, bool wrap, int S,
+                                                             const __grid_constant__ FieldF ff,
+                                                             const __grid_constant__ FieldD fd, double inv_h,
+                                                             const int64_t *__restrict__ d_n, float *__restrict__ dpos,
+                                                             double *__restrict__ partial, int *__restrict__ status)
+{
     constexpr int kW = 2 + 2 * kMaxSpecies * kMaxSpecies;
-    __shared__ Runs runs;
-    __shared__ double red[8][kW];
+    extern __shared__ __align__(128) unsigned char dyn[];
+    NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
+    __shared__ double red[kNbWarps][kW];
+    __shared__ double fpart[kPChunk][3];
+    __shared__ uint4 home[kPChunk];
+    __shared__ long long base_s[kMaxSpecies];  // first species-major row of each species
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int width = 2 + 2 * S * S;
-    __shared__ long long base_s[kMaxSpecies];  // first species-major row of each species
     if (threadIdx.x == 0) {
         long long b = 0;
         for (int s = 0; s < kMaxSpecies; ++s) {
             base_s[s] = b;
             b += (s < S) ? d_n[s] : 0;
         }
+        mbar_init(&sh.bar, 1);
     }
-    for (int k = threadIdx.x; k < 8 * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
+    for (int k = threadIdx.x; k < kNbWarps * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
     __syncthreads();
+    unsigned parity = 0;
+    NbQueue Q = {sh.q[w], 0, 0};
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
-        const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
-        if (w == 0) warp_runs(cs, T, cx, cy, cz, runs);
-        __syncthreads();
-        const int total = runs.end[17];
-        const int h0 = cs[c], h1 = cs[c + 1];
-        for (int i = h0 + w; i < h1; i += 8) {
-            const uint4 p = cpos[i];
-            const int t = (int)tag_species(p.w);
-            R fx = 0, fy = 0, fz = 0;
-            R aE = 0, aW = 0, aEps[NS], aSig[NS];
+        const int h0 = cs[c], nh = cs[c + 1] - h0;
+        if (nh > 0) {
+            const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
+            __syncthreads();
+            if (w == 0) runs27(cs, T, cx, cy, cz, sh.runs);
+            __syncthreads();
+            const int total = sh.runs.end[17];
+            const uint32_t cx0 = cell_centre(cx, T), cy0 = cell_centre(cy, T), cz0 = cell_centre(cz, T);
+            for (int pb = 0; pb < nh; pb += kPChunk) {
+                const int pn = min(kPChunk, nh - pb);
+                __syncthreads();
+                for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+                    home[i] = cpos[h0 + pb + i];
+                    fpart[i][0] = fpart[i][1] = fpart[i][2] = 0.0;
+                }
+                for (int base = 0; base < total; base += kBuf) {
+                    const int nst = min(kBuf, total - base);
+                    if (!nb_stage(sh, cpos, base, base + nst, cx0, cy0, cz0, parity, status)) return;
+                    for (int i = w; i < pn; i += kNbWarps) {
+                        GradDrain<F32, NS> D(sh, ff, fd);
+                        D.P = home[i];
+                        D.t = (int)tag_species(D.P.w);
+                        const uint32_t self = D.P.w;
+                        const float3 pf =
+                            make_float3(rel_f(D.P.x, cx0), rel_f(D.P.y, cy0), rel_f(D.P.z, cz0));
+                        nb_screen(sh, nst, D.P, pf, R2, r2lo, r2hi, wrap, Q,
+                                  [&](int, uint32_t tag) { return tag == self; }, D);
+                        nb_flush(Q, D);
+                        const double gx = warp_sum((double)D.fx), gy = warp_sum((double)D.fy),
+                                     gz = warp_sum((double)D.fz);
+                        double vE, vW;
+                        if constexpr (F32) {
+                            const FF s = ff_warp_sum(FF{D.eh, D.el});
+                            const FF v = ff_warp_sum(FF{D.wh, D.wl});
+                            vE = (double)s.hi + (double)s.lo;
+                            vW = (double)v.hi + (double)v.lo;
+                        } else {
+                            vE = warp_sum(D.de);
+                            vW = warp_sum(D.dw);
+                        }
+                        double ve[NS], vs[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) aEps[q] = aSig[q] = 0;
-            int r = 0;
-            for (int g = lane; g < total; g += 32) {
-                while (g >= runs.end[r]) ++r;
-                const uint4 qv = cpos[runs.start[r] + g - (r ? runs.end[r - 1] : 0)];
-                if (qv.w == p.w) continue;
-                const GridSep sp = grid_sep(p, qv);
-                if (sp.g >= R2) continue;
-                const int ts = (int)tag_species(qv.w);
-                const int k = t * kMaxSpecies + ts;
-                const R ddx = (R)sp.dx, ddy = (R)sp.dy, ddz = (R)sp.dz;
-                const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                const R c4e = F32 ? (R)ff.c4e[k] : (R)fd.c4e[k];
-                const R sig2 = F32 ? (R)ff.sig2[k] : (R)fd.sig2[k];
-                const R s2 = sig2 / r2;
-                const R s6 = s2 * s2 * s2;
-                const R rep = c4e * s6 * s6, att = c4e * s6;
-                const R rdu = (R)(-12) * rep + (R)6 * att;  // r U'(r)
-                const R coef = rdu / r2;
-                fx += coef * ddx;
-                fy += coef * ddy;
-                fz += coef * ddz;
-                const R ue = (R)0.5 * (rep - att);
-                const R uw = (R)0.5 * rdu;
-                const R ge = (R)2 * (s6 * s6 - s6);
-                const R gs = (R)0.5 * ((R)12 * rep - (R)6 * att);
-                aE += ue;
-                aW += uw;
+                        for (int q = 0; q < NS; ++q) {
+                            ve[q] = warp_sum((double)D.aEps[q]);
+                            vs[q] = warp_sum((double)D.aSig[q]);
+                        }
+                        if (lane == 0) {
+                            fpart[i][0] += gx;
+                            fpart[i][1] += gy;
+                            fpart[i][2] += gz;
+                            red[w][0] += vE;
+                            red[w][1] += vW;
 #pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    if (q == ts) {
-                        aEps[q] += ge;
-                        aSig[q] += gs;
+                            for (int q = 0; q < NS; ++q) {
+                                if (q < S) {
+                                    red[w][2 + D.t * S + q] += ve[q];
+                                    red[w][2 + S * S + D.t * S + q] += vs[q];
+                                }
+                            }
+                        }
                     }
                 }
-            }
-            const double gx = warp_sum((double)fx), gy = warp_sum((double)fy), gz = warp_sum((double)fz);
-            if (lane == 0 && dpos) {
-                const int64_t row = base_s[t] + tag_index(p.w);
-                dpos[3 * row + 0] = (float)(gx * inv_h);
-                dpos[3 * row + 1] = (float)(gy * inv_h);
-                dpos[3 * row + 2] = (float)(gz * inv_h);
-            }
-            const R vE = warp_sum(aE), vW = warp_sum(aW);
-            R ve[NS], vs[NS];
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                ve[q] = warp_sum(aEps[q]);
-                vs[q] = warp_sum(aSig[q]);
-            }
-            if (lane == 0) {
-                red[w][0] += (double)vE;
-                red[w][1] += (double)vW;
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    if (q < S) {
-                        red[w][2 + t * S + q] += (double)ve[q];
-                        red[w][2 + S * S + t * S + q] += (double)vs[q];
+                __syncthreads();
+                if (dpos) {
+                    for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+                        const uint32_t tg = home[i].w;
+                        const int64_t row = base_s[tag_species(tg)] + tag_index(tg);
+                        dpos[3 * row + 0] = (float)(fpart[i][0] * inv_h);
+                        dpos[3 * row + 1] = (float)(fpart[i][1] * inv_h);
+                        dpos[3 * row + 2] = (float)(fpart[i][2] * inv_h);
                     }
                 }
             }
@@ -408,12 +715,11 @@ __global__ void __launch_bounds__(256) k_cell_grad(const uint4 *__restrict__ cpo
         __syncthreads();
         if (threadIdx.x < width) {
             double s = 0.0;
-            for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+            for (int k = 0; k < kNbWarps; ++k) s += red[k][threadIdx.x];
             partial[c * width + threadIdx.x] = s;
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < 8 * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
-        __syncthreads();
+        for (int k = threadIdx.x; k < kNbWarps * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
     }
 }
 
@@ -425,26 +731,96 @@ static unsigned blocks_for(gcmc_ctx *ctx, int64_t work, int per_block)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// The screen's band around the grid cutoff R2: FP32 squared distances below
+// r2lo are inside, above r2hi outside; in between the exact integer test
+// decides.  The FP32 separations carry a relative error below 1e-6 of the
+// cell edge (coordinates relative to the cell centre), far inside the band.
+// wrap: the cells are narrower than rc (2 rc <= L < 3 rc), so the FP32
+// separations need their own periodic wrap.
+static void screen_band(const gcmc_ctx *ctx, float &r2lo, float &r2hi, bool &wrap)
+{
+    r2lo = (float)((double)ctx->R2 * (1.0 - 1e-5));
+    r2hi = (float)((double)ctx->R2 * (1.0 + 1e-5));
+    wrap = (double)ctx->T * ctx->rc > ctx->L;
+}
+
+// Grid size of a neighbourhood kernel: one CTA per cell, at most what stays
+// resident (6 CTAs of 8 warps and ~35 KB per SM) times a few waves.
+static unsigned nb_blocks(const gcmc_ctx *ctx, int64_t cells)
+{
+    const int64_t cap = (int64_t)ctx->num_sms * 6 * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cells, cap));
+}
+
+// The neighbourhood kernels take more than 48 KB of shared memory.
+template <typename K>
+static gcmc_status nb_smem(gcmc_ctx *ctx, K kern)
+{
+    const cudaError_t e =
+        cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NbShared));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute (neighbourhood kernel)");
+    return GCMC_OK;
+}
+
 gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *species, const int64_t *exclude,
                          int64_t m, double *out, double *out_abs)
 {
     gcmc_status st = make_compact(ctx);
     if (st != GCMC_OK) return st;
-    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-    const unsigned nb = blocks_for(ctx, m, 8);
-    if (ctx->precision == GCMC_FP32)
-        k_trial_energy<true><<<nb, 256, 0, ctx->stream>>>(pos, species, exclude, m, ctx->cpos, ctx->cell_start,
-                                                         ctx->T, ctx->q, ctx->R2, ctx->S, ctx->ff, ctx->fd, out,
-                                                         out_abs, ctx->d_status);
-    else
-        k_trial_energy<false><<<nb, 256, 0, ctx->stream>>>(pos, species, exclude, m, ctx->cpos, ctx->cell_start,
-                                                          ctx->T, ctx->q, ctx->R2, ctx->S, ctx->ff, ctx->fd, out,
-                                                          out_abs, ctx->d_status);
-    ctx->launches += 1;
+    if (m <= 0) return GCMC_OK;
+    if (m > (int64_t)INT32_MAX) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_trial_energy: too many points");
+    cudaStream_t s = ctx->stream;
+    // scratch: binned points, unbinned points, cell ids, per-cell counts and
+    // starts, fill counters, scan partials
+    const int64_t ncell = ctx->ncell;
+    const int64_t nbs = (ncell + 1023) / 1024 + 1;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_pts = al(m * sizeof(TrialPt)), b_tmp = b_pts, b_cid = al(m * sizeof(int32_t)),
+                 b_cnt = al(ncell * sizeof(int32_t)), b_ps = al((ncell + 1) * sizeof(int32_t)),
+                 b_part = al(nbs * sizeof(int32_t) + 64);
+    st = ensure_scratch(ctx, b_pts + b_tmp + b_cid + 2 * b_cnt + b_ps + b_part);
+    if (st != GCMC_OK) return st;
+    char *p = (char *)ctx->scratch;
+    TrialPt *pts = (TrialPt *)p;
+    TrialPt *tmp = (TrialPt *)(p += b_pts);
+    int32_t *cid = (int32_t *)(p += b_tmp);
+    int32_t *cnt = (int32_t *)(p += b_cid);
+    int32_t *fill = (int32_t *)(p += b_cnt);
+    int32_t *ps = (int32_t *)(p += b_cnt);
+    int32_t *part = (int32_t *)(p += b_ps);
+    int *vmax = part + nbs;
+    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    GCMC_CUDA(ctx, cudaMemsetAsync(cnt, 0, 2 * b_cnt, s));  // counts and fill counters
+    const unsigned gb = blocks_for(ctx, m, 256);
+    k_trial_bin<<<gb, 256, 0, s>>>(pos, species, exclude, m, ctx->q, ctx->T, ctx->S, tmp, cid, cnt, out, out_abs,
+                                   ctx->d_status);
+    st = exclusive_scan(ctx, cnt, ncell, ps, part, vmax);
+    if (st != GCMC_OK) return st;
+    k_trial_place<<<gb, 256, 0, s>>>(tmp, cid, m, ps, fill, pts);
+    float r2lo, r2hi;
+    bool wrap;
+    screen_band(ctx, r2lo, r2hi, wrap);
+    const unsigned nb = nb_blocks(ctx, ncell);
+    if (ctx->precision == GCMC_FP32) {
+        st = nb_smem(ctx, k_trial_energy<true>);
+        if (st != GCMC_OK) return st;
+        k_trial_energy<true><<<nb, kNbWarps * 32, sizeof(NbShared), s>>>(
+            pts, ps, ctx->cpos, ctx->cell_start, ctx->T, ncell, ctx->R2, r2lo, r2hi, wrap, ctx->ff, ctx->fd, out, out_abs,
+            ctx->d_status);
+    } else {
+        st = nb_smem(ctx, k_trial_energy<false>);
+        if (st != GCMC_OK) return st;
+        k_trial_energy<false><<<nb, kNbWarps * 32, sizeof(NbShared), s>>>(
+            pts, ps, ctx->cpos, ctx->cell_start, ctx->T, ncell, ctx->R2, r2lo, r2hi, wrap, ctx->ff, ctx->fd, out, out_abs,
+            ctx->d_status);
+    }
+    ctx->launches += 3;
     GCMC_CUDA(ctx, cudaGetLastError());
     int bits = 0;
     st = read_status(ctx, &bits);
     if (st != GCMC_OK) return st;
+    if (bits & kStatusTimeout)
+        return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_trial_energy: a bulk copy did not complete within the wait limit");
     if (bits & kStatusBadInput)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_trial_energy: species out of range or coordinate not finite");
     return GCMC_OK;
@@ -456,20 +832,35 @@ gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
     if (st != GCMC_OK) return st;
     st = ensure_red(ctx, 2 * (size_t)ctx->ncell + 8);
     if (st != GCMC_OK) return st;
-    const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
-    if (ctx->precision == GCMC_FP32)
-        k_cell_energy<true><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2,
-                                                        ctx->ff, ctx->fd, ctx->d_red);
-    else
-        k_cell_energy<false><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2,
-                                                         ctx->ff, ctx->fd, ctx->d_red);
+    float r2lo, r2hi;
+    bool wrap;
+    screen_band(ctx, r2lo, r2hi, wrap);
+    const unsigned nb = nb_blocks(ctx, ctx->ncell);
+    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    if (ctx->precision == GCMC_FP32) {
+        st = nb_smem(ctx, k_cell_energy<true>);
+        if (st != GCMC_OK) return st;
+        k_cell_energy<true><<<nb, kNbWarps * 32, sizeof(NbShared), ctx->stream>>>(
+            ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, r2lo, r2hi, wrap, ctx->ff, ctx->fd, ctx->d_red,
+            ctx->d_status);
+    } else {
+        st = nb_smem(ctx, k_cell_energy<false>);
+        if (st != GCMC_OK) return st;
+        k_cell_energy<false><<<nb, kNbWarps * 32, sizeof(NbShared), ctx->stream>>>(
+            ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, r2lo, r2hi, wrap, ctx->ff, ctx->fd, ctx->d_red,
+            ctx->d_status);
+    }
     k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 2, ctx->d_red + 2 * ctx->ncell);
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());
-    double ew[2] = {0.0, 0.0};
+    double ew[3] = {0.0, 0.0, 0.0};
     GCMC_CUDA(ctx, cudaMemcpyAsync(ew, ctx->d_red + 2 * ctx->ncell, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
+    int bits = 0;
+    GCMC_CUDA(ctx, cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bits & kStatusTimeout)
+        return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_total_energy: a bulk copy did not complete within the wait limit");
     const double e = ew[0];
     ctx->virial = ew[1];
     ctx->virial_valid = true;
@@ -497,12 +888,21 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
     const int width = 2 + 2 * S * S;
     st = ensure_red(ctx, (size_t)ctx->ncell * width + width);
     if (st != GCMC_OK) return st;
-    const unsigned nb = (unsigned)std::min<int64_t>(ctx->ncell, (int64_t)ctx->num_sms * 8);
+    float r2lo, r2hi;
+    bool wrap;
+    screen_band(ctx, r2lo, r2hi, wrap);
+    const unsigned nb = nb_blocks(ctx, ctx->ncell);
     double *part = ctx->d_red;
     double *res = ctx->d_red + (size_t)ctx->ncell * width;
-#define GCMC_GRAD(F, NSP)                                                                                   \
-    k_cell_grad<F, NSP><<<nb, 256, 0, ctx->stream>>>(ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, S, \
-                                                     ctx->ff, ctx->fd, 1.0 / ctx->h, ctx->d_n, dpos, part)
+    GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+#define GCMC_GRAD(F, NSP)                                                                                     \
+    do {                                                                                                      \
+        st = nb_smem(ctx, k_cell_grad<F, NSP>);                                                               \
+        if (st != GCMC_OK) return st;                                                                         \
+        k_cell_grad<F, NSP><<<nb, kNbWarps * 32, sizeof(NbShared), ctx->stream>>>(                            \
+            ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, r2lo, r2hi, wrap, S, ctx->ff, ctx->fd,    \
+            1.0 / ctx->h, ctx->d_n, dpos, part, ctx->d_status);                                               \
+    } while (0)
     if (ctx->precision == GCMC_FP32) {
         if (S == 1) GCMC_GRAD(true, 1);
         else if (S == 2) GCMC_GRAD(true, 2);
@@ -517,8 +917,12 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());
     double h[2 + 2 * kMaxSpecies * kMaxSpecies];
+    int bits = 0;
     GCMC_CUDA(ctx, cudaMemcpyAsync(h, res, width * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GCMC_CUDA(ctx, cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bits & kStatusTimeout)
+        return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_energy_grad: a bulk copy did not complete within the wait limit");
     if (energy) *energy = h[0];
     if (virial) *virial = h[1];
     for (int a = 0; a < S; ++a)
@@ -541,6 +945,7 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
 // context's scratch.  The array is shared by every call on a device: two
 // calls whose kernels overlap on the GPU race on it.
 // ---------------------------------------------------------------------------
+constexpr int kStage = 2048;  // staged partners per pass (32 KB)
 constexpr int64_t kStaticMaxCells = GCMC_NOALLOC_MAX_CELLS;  // T <= 50; 1 MiB of partials
 static __device__ __align__(256) double g_static_partials[kStaticMaxCells];
 

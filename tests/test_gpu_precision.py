@@ -125,10 +125,11 @@ def test_du_error_isotherm_64_chains():
     FP32 pair terms), 20,000 moves per chain: every chain equals the oracle's
     chain k move for move, and every move's dU error is <= 1e-5."""
     chains = W.isotherm_chains()
-    boxes, mixes, seeds = [], [], []
+    boxes, mixes, seeds, e0 = [], [], [], []
     for k, w in enumerate(chains):
         b = Box(w.L, w.rc, w.eps, w.sigma, precision="fp32")
         b.build_cells(torch.as_tensor(w.positions()), torch.as_tensor(w.types()))
+        e0.append(b.total_energy())  # the chain's starting energy
         boxes.append(b)
         mixes.append(Mix(*_mixargs(w)))
         seeds.append(w.seed)
@@ -142,13 +143,14 @@ def test_du_error_isotherm_64_chains():
         o = O.System(w.L, w.rc, w.eps, w.sigma)
         o.build(w.positions(), w.types())
         o.set_energy(o.total_energy())
+        start = o.energy()
         to, so, sabs = o.run_moves(w.seed, 0, n, *_mixargs(w), tol=1e-5, chain=k, with_sabs=True)
-        return to, so, sabs, o.state()
+        return to, so, sabs, o.state(), start
 
     with cf.ThreadPoolExecutor(max_workers=16) as ex:  # the oracle's C calls release the GIL
         refs = list(ex.map(oracle_chain, range(len(chains))))
     worst = 0.0
-    for k, (to, so, sabs, st_o) in enumerate(refs):
+    for k, (to, so, sabs, st_o, start) in enumerate(refs):
         err, stop = du_errors(traces[k], to, sabs)
         assert stop == n, k
         worst = max(worst, float(err.max()))
@@ -156,7 +158,11 @@ def test_du_error_isotherm_64_chains():
         st_g = boxes[k].get_state()
         for x, y in zip(st_o, st_g[:4]):
             assert np.array_equal(x, y), k
-        assert abs(stats[k]["energy"] - so.energy) <= 1e-10 * to["uabs"].sum() + 1e-9
+        # the chain's own change of the running energy (the starting values
+        # are full-system energies, compared in their own tests)
+        acc = to["accepted"] == 1
+        assert abs((stats[k]["energy"] - e0[k]) - (so.energy - start)) <= \
+            1e-10 * to["uabs"][acc].sum() + 1e-12 * (abs(start) + abs(e0[k])) + 1e-9
     assert worst <= 1e-5, worst
 
 
@@ -232,7 +238,8 @@ def test_gradient_262144_subset(precision):
     sm = species_major_order(types)
     # analytic: species-major rows of the GPU result against the oracle's
     fs = np.abs(ref["dpos"][rows]).max()
-    tol = 1e-5 if precision == "fp32" else 1e-9
+    # dpos is returned as FP32 in both modes: FP64 mode carries its rounding
+    tol = 1e-5 if precision == "fp32" else 2e-7
     assert np.allclose(dpos[rows], ref["dpos"][rows], rtol=tol, atol=tol * fs)
     for k in ("deps", "dsigma"):
         assert np.allclose(g[k], ref[k], rtol=10 * TOL[precision])

@@ -324,6 +324,18 @@ gcmc_status gcmc_kernel_launches(gcmc_ctx *ctx, int64_t *out);
  * Errors: INVALID_ARG. */
 gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refined);
 
+/* Where the chain kernel's time went in the last gcmc_run_moves (or batch
+ * run) of this context, in SM clock cycles summed over the run (host, 12
+ * doubles): [0] the committer waiting for evaluations, [1] checking their
+ * validity, [2] deciding (partial sums, Metropolis test, FP64 refinement),
+ * [3] applying accepted moves, [4] the committer's whole loop; [5] the team
+ * leaders waiting for an eligible move and [6] the teams evaluating (summed
+ * over teams), [7] evaluations; [8] .. [10] the parts of [1]: the count
+ * epoch, the logged moves, the particle pick; [11] booking a decided move.
+ * Zeros for the microcell chain.
+ * Errors: INVALID_ARG. */
+gcmc_status gcmc_chain_profile(gcmc_ctx *ctx, double *cycles);
+
 /* Team shape of the chain kernel (how its warps split the evaluation of
  * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape
  * during the next gcmc_run_moves (after a first quarter of its moves under

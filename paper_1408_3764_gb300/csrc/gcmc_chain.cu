@@ -61,6 +61,14 @@ struct ChainOut {
     double virial;          // running virial after the last move (virial runs)
     double sum_virial;      // sum over the moves of the running virial
     unsigned long long t0, t1;  // global timer (ns) when the chain's CTA started and finished
+    // SM clock cycles summed over the moves: the committer waiting for
+    // evaluations, checking their validity, deciding (partial sums,
+    // Metropolis test, FP64 refinement), applying accepted moves, and its
+    // whole loop; the team leaders waiting for an eligible move and the teams
+    // evaluating (summed over teams and evaluations); evaluations
+    // then the validity check's parts: the count epoch, the logged moves,
+    // the particle pick; and the booking of a decided move
+    unsigned long long prof[12];
 };
 
 struct ChainArgs {
@@ -189,17 +197,21 @@ struct Slot {  // evaluators -> committer, one per move in flight
     int arrive;                   // warps finished
     int tag;                      // move + 1 of the evaluation under way, 0 none
     int pseq[kGMax];              // per warp: count epoch its work-cell counts were read in (-1 torn)
+    int nsu[kMaxSpecies];         // the particle counts the evaluation picked its particle with
+    int acc0;                     // accepted moves (at most) when the evaluation started
+    // the team's totals, summed by its last warp to arrive (fixed order)
+    float th, tl, tu, tw;         // FP32: dU (hi, lo), uabs, virial change
+    double td, ta, tdw;           // FP64: dU, uabs, virial change
     int pad[2];
 };
 
-struct LogRec {  // committer -> evaluation validity
-    int flags;         // bit0 accepted, bit1 N changed
-    int mx[3], my[3], mz[3];  // cells written (-1 none)
-    int ids[3];        // (s << 24) | index of records written
-    int np;            // positions that gained or lost a particle
-    int has_moved;     // a removal moved the cell's last entry into the freed slot
-    uint4 pos[2];
-    uint4 moved;       // that entry
+struct __align__(16) LogRec {  // committer -> evaluation validity (five 16-byte words)
+    int4 head;    // x: flags (bit0 accepted, bit1 N changed); y, z, w: cells written (-1 none)
+    int4 ids;     // x, y, z: (s << 24) | index of the records written (-1 none);
+                  // w: positions that gained or lost a particle (np) | has_moved << 8 (a removal
+                  //    moved the cell's last entry into the freed slot)
+    uint4 pos0, pos1;
+    uint4 moved;  // that entry
 };
 
 struct BookRec {  // committer -> keeper
@@ -226,7 +238,7 @@ struct __align__(16) Shared {
     long long n[kMaxSpecies];
     float ln_n[kMaxSpecies];
     float ln_n1[kMaxSpecies];
-    int ns_ring[kRS][kMaxSpecies];  // N_s after c commits, at [c % kRS]
+    int ns_ring[kRS][kMaxSpecies];  // N_s after c commits, at [(c) & (kRS - 1)]
     int committed;  // moves committed
     int filled;     // words available for moves < filled
     int booked;     // moves the keeper has processed
@@ -240,6 +252,7 @@ struct __align__(16) Shared {
     // (the bet the count prediction makes on moves not yet evaluated)
     int likely[2];
     int never;  // a flag nothing sets (the diagnostic stall waits on it)
+    int nacc;   // moves accepted so far (published before the commit count)
 };
 
 __device__ __forceinline__ int vload(const int &x) { return *(volatile const int *)&x; }
@@ -276,13 +289,13 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
 // The Metropolis test of Eqs. 3-5 (textbook sign of mu) in FP32 with an
 // explicit error band: 1 accept, 0 reject, -1 inside the band or not finite
 // (the caller decides in FP64).  ns: N_s before the move.
-__device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, int ns, float lnu, float dUf,
-                                          float uab)
+__device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, float ln_ns, float ln_ns1, float lnu,
+                                          float dUf, float uab)
 {
     const float beta_f = (float)a.beta, tol_f = (float)a.tol;
     float lnK = 0.f;
-    if (type == 1) lnK = a.lnzv_f[sp] - logf((float)(ns + 1));
-    else if (type == 2) lnK = logf((float)ns) - a.lnzv_f[sp];
+    if (type == 1) lnK = a.lnzv_f[sp] - ln_ns1;
+    else if (type == 2) lnK = ln_ns - a.lnzv_f[sp];
     const float lnA = lnK - beta_f * dUf;
     const float band = beta_f * tol_f * uab + 1e-6f * (1.f + fabsf(lnK) + fabsf(beta_f * dUf) + fabsf(lnu));
     const float diff = lnu - lnA;
@@ -293,14 +306,17 @@ __device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, 
 // ---------------------------------------------------------------- the chain
 // VIR: the evaluations also sum the virial change dW of each trial.
 constexpr int kQ = 64;  // entries of an evaluator warp's queue of pair terms inside the cutoff
+constexpr int kChainWarps = 16;  // warps of a chain CTA (committer, keeper, evaluators, idle)
 
 template <bool F32, bool VIR>
 struct Chain {
     const ChainArgs &a;
     Shared &sh;
     uint16_t *cnt;
-    int4 *fq;  // kQ entries per evaluator warp (warps 1 .. EW)
+    int4 *fq;  // kQ entries per evaluator warp
     int lane, warp, T;
+    int eidx = 0;  // this warp's index among the evaluator warps
+    int first_mod;  // first move of the launch modulo the words ring
     uint32_t uT;
 
     __device__ Chain(const ChainArgs &a_, Shared &sh_, uint16_t *cnt_, int4 *fq_) : a(a_), sh(sh_), cnt(cnt_), fq(fq_)
@@ -309,11 +325,12 @@ struct Chain {
         warp = threadIdx.x >> 5;
         T = a.T;
         uT = (uint32_t)a.T;
+        first_mod = (int)(a.first & (uint64_t)(kRW - 1));
     }
 
     __device__ __forceinline__ const WordRec &words(int m) const
     {
-        return sh.words[(int)((a.first + (uint64_t)m) % kRW)];
+        return sh.words[(first_mod + m) & (kRW - 1)];
     }
 
     // the trial of move m given the particle counts ns[] (warp-uniform)
@@ -614,7 +631,7 @@ struct Chain {
         o.has_last = 0;
         o.last = make_uint4(0, 0, 0, 0);
         Acc32 A = {0.f, 0.f, 0.f, 0.f};
-        FQ Q = {P32 ? fq + (warp - 1) * kQ : nullptr, 0, 0};
+        FQ Q = {P32 ? fq + eidx * kQ : nullptr, 0, 0};
         double de = 0.0, da = 0.0, dw = 0.0;
         const int nw = nwork(t);
         AxisList X, Y, Z;
@@ -723,7 +740,7 @@ struct Chain {
             const uint64_t m = a.first + (uint64_t)(m0 + lane);
             const uint4 r0 = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, 0u), key);
             const uint4 r1 = philox_block(make_uint4((uint32_t)m, (uint32_t)(m >> 32), a.chain, 1u), key);
-            WordRec &W = sh.words[(int)(m % kRW)];
+            WordRec &W = sh.words[(int)(m & (uint64_t)(kRW - 1))];
             W.w[0] = r0.x;
             W.w[1] = r0.y;
             W.w[2] = r0.z;
@@ -750,49 +767,44 @@ struct Chain {
         __threadfence_block();
     }
 
-    __device__ __forceinline__ void note(LogRec &L, int &nm, int x, int y, int z) const
-    {
-        L.mx[nm] = x;
-        L.my[nm] = y;
-        L.mz[nm] = z;
-        ++nm;
-    }
 
-    // Committer: apply an accepted move (Sec. 3.2.5), log what it changed.
+    // Committer: apply an accepted move (Sec. 3.2.5), log what it changed
+    // (gathered in registers, stored as five 16-byte words).
     __device__ __forceinline__ void apply(const Trial &t, int self_slot, const uint4 &last_val, LogRec &L) const
     {
         const int sp = t.s;
         const long long sb = (long long)sp * a.maxN;
-        int nm = 0, nid = 0;
+        int cells[3] = {-1, -1, -1}, ids[3] = {-1, -1, -1};
+        int np = 0, has_moved = 0;
+        uint4 pos0 = make_uint4(0, 0, 0, 0), pos1 = pos0, moved = pos0;
         if (t.type != 2) {
             if (lane == 0) {
-                L.has_moved = 0;
                 if (t.type == 0) {
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, t.Po.w);
                     if (!t.cross) {
                         a.cell_pos[(long long)t.co * a.cap + self_slot] = v;
-                        note(L, nm, t.px, t.py, t.pz);
+                        cells[0] = t.co;
                     } else {
                         seq_bump();
                         const int c_o = cnt[t.co];
                         if (self_slot != c_o - 1) {
                             a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
-                            L.has_moved = 1;
-                            L.moved = last_val;
+                            has_moved = 1;
+                            moved = last_val;
                         }
                         cnt[t.co] = (uint16_t)(c_o - 1);
                         const int c_n = cnt[t.cn];
                         a.cell_pos[(long long)t.cn * a.cap + c_n] = v;
                         cnt[t.cn] = (uint16_t)(c_n + 1);
                         seq_bump();
-                        note(L, nm, t.px, t.py, t.pz);
-                        note(L, nm, t.qx, t.qy, t.qz);
+                        cells[0] = t.co;
+                        cells[1] = t.cn;
                     }
-                    L.pos[0] = t.Po;
-                    L.pos[1] = t.Pn;
-                    L.np = 2;
+                    pos0 = t.Po;
+                    pos1 = t.Pn;
+                    np = 2;
                     a.pos_by_id[sb + t.idx] = v;
-                    L.ids[nid++] = (sp << 24) | t.idx;
+                    ids[0] = (sp << 24) | t.idx;
                 } else {
                     const long long ni = sh.n[sp];
                     const uint4 v = make_uint4(t.Pn.x, t.Pn.y, t.Pn.z, make_tag((uint32_t)ni, (uint32_t)sp));
@@ -805,39 +817,36 @@ struct Chain {
                     sh.n[sp] = ni + 1;
                     sh.ln_n[sp] = logf((float)(ni + 1));
                     sh.ln_n1[sp] = logf((float)(ni + 2));
-                    note(L, nm, t.qx, t.qy, t.qz);
-                    L.ids[nid++] = (sp << 24) | (int)ni;
-                    L.pos[0] = t.Pn;
-                    L.np = 1;
+                    cells[0] = t.cn;
+                    ids[0] = (sp << 24) | (int)ni;
+                    pos0 = t.Pn;
+                    np = 1;
                 }
-                for (int q = nm; q < 3; ++q) L.mx[q] = -1;
-                for (int q = nid; q < 3; ++q) L.ids[q] = -1;
-                L.flags = 1 | ((t.type == 1) ? 2 : 0);
+                L.ids = make_int4(ids[0], ids[1], ids[2], np | (has_moved << 8));
+                L.pos0 = pos0;
+                L.pos1 = pos1;
+                L.moved = moved;
+                L.head = make_int4(1 | ((t.type == 1) ? 2 : 0), cells[0], cells[1], cells[2]);
             }
             return;
         }
         // deletion: swap-with-last inside the cell, then the species' last
         // index takes the freed index (its record and its cell entry)
         const long long last = sh.n[sp] - 1;
-        int swapped = 0;
         if (lane == 0) {
             seq_bump();
             const int c_o = cnt[t.co];
-            swapped = self_slot != c_o - 1;
-            if (swapped) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
+            has_moved = self_slot != c_o - 1;
+            if (has_moved) a.cell_pos[(long long)t.co * a.cap + self_slot] = last_val;
             cnt[t.co] = (uint16_t)(c_o - 1);
             seq_bump();
-            L.has_moved = swapped;
-            L.moved = last_val;
+            moved = last_val;
         }
         __syncwarp();
-        int qx = -1, qy = 0, qz = 0;
+        int cq = -1;
         if (t.idx != last) {
             const uint4 Q = a.pos_by_id[sb + last];
-            qx = cell_coord(Q.x, uT);
-            qy = cell_coord(Q.y, uT);
-            qz = cell_coord(Q.z, uT);
-            const int cq = (qz * T + qy) * T + qx;
+            cq = (cell_coord(Q.z, uT) * T + cell_coord(Q.y, uT)) * T + cell_coord(Q.x, uT);
             const int cc = cnt[cq];
             const uint32_t ntag = make_tag((uint32_t)t.idx, (uint32_t)sp);
             for (int base = 0; base < cc; base += 32) {
@@ -851,17 +860,17 @@ struct Chain {
             if (lane == 0) a.pos_by_id[sb + t.idx] = make_uint4(Q.x, Q.y, Q.z, ntag);
         }
         if (lane == 0) {
-            note(L, nm, t.px, t.py, t.pz);
-            L.pos[0] = t.Po;
-            L.np = 1;
-            L.ids[nid++] = (sp << 24) | t.idx;
-            if (qx >= 0) {
-                note(L, nm, qx, qy, qz);
-                L.ids[nid++] = (sp << 24) | (int)last;
+            cells[0] = t.co;
+            ids[0] = (sp << 24) | t.idx;
+            if (cq >= 0) {
+                cells[1] = cq;
+                ids[1] = (sp << 24) | (int)last;
             }
-            for (int q = nm; q < 3; ++q) L.mx[q] = -1;
-            for (int q = nid; q < 3; ++q) L.ids[q] = -1;
-            L.flags = 3;
+            L.ids = make_int4(ids[0], ids[1], ids[2], 1 | (has_moved << 8));
+            L.pos0 = t.Po;
+            L.pos1 = make_uint4(0, 0, 0, 0);
+            L.moved = moved;
+            L.head = make_int4(3, cells[0], cells[1], cells[2]);
             sh.n[sp] = last;
             sh.ln_n[sp] = logf((float)last);
             sh.ln_n1[sp] = logf((float)(last + 1));
@@ -884,82 +893,101 @@ __device__ __forceinline__ long long axis_gap(uint32_t a0, uint32_t a1, uint32_t
     return lo > 0 ? lo : (hi < 0 ? -hi : 0);
 }
 
-__device__ __forceinline__ bool box_within(const uint4 &X0, const uint4 &X1, const uint4 &P, unsigned long long R2)
+// |a - p| along an axis, the minimum image as an unsigned 32-bit distance.
+__device__ __forceinline__ uint32_t axis_dist(uint32_t a, uint32_t p)
 {
+    const uint32_t d = a - p;
+    return (d & 0x80000000u) ? 0u - d : d;
+}
+
+__device__ __forceinline__ bool box_within(const uint4 &X0, const uint4 &X1, const uint4 &P, unsigned long long R2,
+                                           uint32_t rcg)
+{
+    // a box whose gap along one axis reaches rcg (rcg^2 >= R2) is out of
+    // reach: for a point record (X0 == X1) that settles most tests in
+    // 32-bit arithmetic
+    const uint32_t g0 = min(axis_dist(X0.x, P.x), axis_dist(X1.x, P.x));
+    const uint32_t g1 = min(axis_dist(X0.y, P.y), axis_dist(X1.y, P.y));
+    const uint32_t g2 = min(axis_dist(X0.z, P.z), axis_dist(X1.z, P.z));
+    if (g0 >= rcg || g1 >= rcg || g2 >= rcg) return false;
     const long long dx = axis_gap(X0.x, X1.x, P.x), dy = axis_gap(X0.y, X1.y, P.y), dz = axis_gap(X0.z, X1.z, P.z);
     return (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy) + (unsigned long long)(dz * dz) < R2;
 }
 
-// Whether a move evaluated after `c0` commits is still valid after `m`: no
-// committed move in [c0, m) touched its cells or wrote its particle's record,
-// and the current particle counts pick the same particle (or, for a move
-// that was impossible, still make it impossible).
+// Whether the committed moves [j0, j1) left a trial's evaluation standing:
+// none of them touched its old cell or wrote its particle's record, and
+// none put, removed or moved a particle within rc of its old or new
+// position.  Warp-wide (one lane per logged move); the result is uniform.
 template <bool F32, bool VIR>
-__device__ __forceinline__ bool still_valid(const Chain<F32, VIR> &C, const Shared &sh, const Trial &t, int c0, int m,
-                                            int T, int lane)
+__device__ __forceinline__ bool logs_ok(const Chain<F32, VIR> &C, const Shared &sh, const Trial &t, int j0, int j1,
+                                        int lane)
 {
     bool bad = false;
-    bool nchanged = false;
     const ChainArgs &a = C.a;
-    for (int j = c0 + lane; j < m; j += 32) {
-        const LogRec &L = sh.logs[j % kRS];
-        const int f = L.flags;
-        if (!(f & 1)) continue;
-        if (f & 2) nchanged = true;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (L.mx[q] >= 0) {
-                // the old cell's slots (self, last entry) must be as seen
-                const int c = (L.mz[q] * T + L.my[q]) * T + L.mx[q];
-                if (t.possible && t.type != 1 && c == t.co) bad = true;
-            }
-            if (t.possible && t.type != 1 && L.ids[q] >= 0 && L.ids[q] == (((int)t.s << 24) | t.idx)) bad = true;
-        }
-        // a particle that appeared, vanished or moved within rc of the
-        // trial's old or new position changes dU (exact integer cutoff, as
-        // in Eq. 1's sum); so may a cell's last entry that a removal moved
-        // into the freed slot (an evaluation that read the older count may
-        // have met it twice).  Changes farther away add nothing: their pair
-        // terms are exactly zero.
-        if (t.possible) {
-            const uint4 X0 = L.pos[0], X1 = (L.np == 2) ? L.pos[1] : L.pos[0];
-            if (t.type != 1 && box_within(X0, X1, t.Po, a.R2)) bad = true;
-            if (t.type != 2 && box_within(X0, X1, t.Pn, a.R2)) bad = true;
-            if (L.has_moved) {
-                if (t.type != 1 && box_within(L.moved, L.moved, t.Po, a.R2)) bad = true;
-                if (t.type != 2 && box_within(L.moved, L.moved, t.Pn, a.R2)) bad = true;
+    if (t.possible) {
+        const bool old_side = t.type != 1, new_side = t.type != 2;
+        const int myid = ((int)t.s << 24) | t.idx;
+        const unsigned long long R2 = a.R2;
+        const uint32_t rcg = (uint32_t)a.rcg;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            // the five words of the log entry, loaded together
+            const LogRec &L = sh.logs[j & (kRS - 1)];
+            const int4 h = L.head, id = L.ids;
+            const uint4 X0 = L.pos0, X1r = L.pos1, Mv = L.moved;
+            if (!(h.x & 1)) continue;
+            const uint4 X1 = ((id.w & 0xFF) == 2) ? X1r : X0;
+            // the old cell's slots (self, last entry) must be as seen, and
+            // the particle's record must be as read
+            if (old_side && (h.y == t.co || h.z == t.co || h.w == t.co || id.x == myid || id.y == myid ||
+                             id.z == myid))
+                bad = true;
+            // a particle that appeared, vanished or moved within rc of the
+            // trial's old or new position changes dU (exact integer cutoff,
+            // as in Eq. 1's sum); so may a cell's last entry that a removal
+            // moved into the freed slot (an evaluation that read the older
+            // count may have met it twice).  Changes farther away add
+            // nothing: their pair terms are exactly zero.
+            if (old_side && box_within(X0, X1, t.Po, R2, rcg)) bad = true;
+            if (new_side && box_within(X0, X1, t.Pn, R2, rcg)) bad = true;
+            if (id.w >> 8) {
+                if (old_side && box_within(Mv, Mv, t.Po, R2, rcg)) bad = true;
+                if (new_side && box_within(Mv, Mv, t.Pn, R2, rcg)) bad = true;
             }
         }
     }
-    if (__any_sync(0xffffffffu, bad)) return false;
-    (void)nchanged;
-    if (t.type != 1) {
-        // the move stands only if the counts at its turn pick the same
-        // particle (the evaluation may have used predicted counts)
-        const int *ns = sh.ns_ring[m % kRS];
-        const WordRec &W = C.words(m);
-        int s = 0, idx = -1, possible = 1;
-        if (t.type == 0) {
-            int N = 0;
-            for (int q = 0; q < C.a.S; ++q) N += ns[q];
-            if (N == 0) {
-                possible = 0;
-            } else {
-                int k = (int)__umulhi(W.w[1], (uint32_t)N);
-                while (k >= ns[s]) {
-                    k -= ns[s];
-                    ++s;
-                }
-                idx = k;
-            }
+    return !__any_sync(0xffffffffu, bad);
+}
+
+// Whether the particle counts at move m's turn pick the particle the
+// evaluation used (it may have used predicted counts), or still make an
+// impossible move impossible.
+template <bool F32, bool VIR>
+__device__ __forceinline__ bool pick_ok(const Chain<F32, VIR> &C, const Shared &sh, const Trial &t, int m)
+{
+    if (t.type == 1) return true;
+    const int *ns = sh.ns_ring[(m) & (kRS - 1)];
+    const WordRec &W = C.words(m);
+    int s = 0, idx = -1, possible = 1;
+    if (t.type == 0) {
+        int N = 0;
+        for (int q = 0; q < C.a.S; ++q) N += ns[q];
+        if (N == 0) {
+            possible = 0;
         } else {
-            s = (int)t.s;
-            if (ns[s] == 0) possible = 0;
-            else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
+            int k = (int)__umulhi(W.w[1], (uint32_t)N);
+            while (k >= ns[s]) {
+                k -= ns[s];
+                ++s;
+            }
+            idx = k;
         }
-        if (possible != (int)t.possible) return false;
-        if (possible && (s != (int)t.s || idx != t.idx)) return false;
+    } else {
+        s = (int)t.s;
+        if (ns[s] == 0) possible = 0;
+        else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
     }
+    if (possible != (int)t.possible) return false;
+    if (possible && (s != (int)t.s || idx != t.idx)) return false;
     return true;
 }
 
@@ -982,11 +1010,13 @@ struct TeamCtl {
 // ahead of the team's new moves.  KU: slots per work cell a lane loads at
 // once.
 template <bool F32, bool VIR, int G, int NTEAM, int LOOK, int KU>
-__global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainArgs *__restrict__ args)
+__global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
     static_assert(G <= kGMax && LOOK < kRS && NTEAM <= 15, "team shape");
     constexpr int EW = G * NTEAM;
-    constexpr int NTH = (EW + 2) * 32;
+    constexpr int NW = kChainWarps;
+    constexpr int NTH = NW * 32;
+    static_assert(EW + 2 <= NW, "team shape");
     extern __shared__ __align__(16) unsigned char dyn[];
     uint16_t *cnt = (uint16_t *)dyn;
     unsigned long long t_start = 0;
@@ -994,6 +1024,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
     __shared__ Shared sh;
     __shared__ TeamCtl ctl[NTEAM];
     __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
+    __shared__ unsigned long long team_cyc[3];  // leaders' idle cycles, evaluation cycles, evaluations
     // this CTA's chain: its arguments copied to shared memory
     __shared__ __align__(16) ChainArgs a;
     {
@@ -1017,7 +1048,17 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
     Chain<F32, VIR> C(a, sh, cnt, fq);
     const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
     const int n = a.n_moves;
-    const int keeper_warp = EW + 1;
+    // Roles by warp.  Warp w runs on the SM sub-partition w % 4, so the
+    // committer (warp 0), whose every step is on the chain's critical path,
+    // shares its sub-partition's issue slots with the keeper (warp 4, mostly
+    // asleep) and at most two evaluator warps (8 and 12, only for teams of
+    // more than 12 warps); the evaluators fill the other sub-partitions first.
+    const int keeper_warp = 4;
+    int eid = -1;
+    if (warp & 3) eid = (warp >> 2) * 3 + (warp & 3) - 1;
+    else if (warp == 8 || warp == 12) eid = 12 + (warp >> 2) - 2;
+    if (eid >= EW) eid = -1;
+    C.eidx = eid;
 
     for (int c = tid; c < a.ncell; c += NTH) cnt[c] = (uint16_t)a.cell_count[c];
     if (tid < kMaxSpecies) {
@@ -1031,9 +1072,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.slots[k].tag = 0;
         sh.slots[k].arrive = 0;
         sh.book[k].ready = 0;
-        sh.logs[k].flags = 0;
+        sh.logs[k].head.x = 0;
     }
     if (tid < NTEAM) redo[tid] = 0;
+    if (tid < 3) team_cyc[tid] = 0ull;
     if (tid == 0) {
         sh.committed = 0;
         sh.booked = 0;
@@ -1043,40 +1085,48 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         sh.seq = 0;
         sh.likely[0] = sh.likely[1] = 0;
         sh.never = 0;
+        sh.nacc = 0;
     }
     {
         const int first_fill = min(n, kRW);
-        for (int b = warp; b * kFill < first_fill; b += EW + 2)
+        for (int b = warp; b * kFill < first_fill; b += NW)
             C.fill_words(b * kFill, min(kFill, first_fill - b * kFill));
         if (tid == 0) sh.filled = first_fill;
     }
     __syncthreads();
 
-    if (warp >= 1 && warp <= EW) {
+    if (eid >= 0) {
         // ------------------------------------------------------------ evaluators
-        const int team = (warp - 1) / G, j = (warp - 1) % G;
+        const int team = eid / G, j = eid % G;
         TeamCtl &tc = ctl[team];
         int next = team;  // the team's next new move (leader lane 0)
+        unsigned long long cyc_idle = 0, cyc_eval = 0, n_eval = 0;  // leader lane of warp j == 0
         for (int it = 0;; ++it) {
             const int p = it & 1;
             if (j == 0 && lane == 0) {
+                const unsigned long long ti = clock64();
                 Wait wt;
-                int go = 0, mm = 0, c0 = 0;
+                int go = 0, mm = 0, c0 = 0, acc0 = 0;
                 for (;;) {
                     if (vload(sh.stop)) {
                         go = 2;
                         break;
                     }
+                    // the accepted count is read before the commit count, so
+                    // that it never covers a commit the evaluation did not see
+                    const int acc_seen = vload(sh.nacc);
+                    __threadfence_block();
                     const int com = vload(sh.committed);
                     const int rd = vload(redo[team]);
                     const bool fresh = next < n && next < com + LOOK && next < vload(sh.filled);
                     if (rd || fresh) {
                         // the counts after `com` commits (the ring entry stays
                         // until com + kRS - 1 moves are committed)
-                        for (int q = 0; q < a.S; ++q) tc.ns[p][q] = sh.ns_ring[com % kRS][q];
+                        for (int q = 0; q < a.S; ++q) tc.ns[p][q] = sh.ns_ring[(com) & (kRS - 1)][q];
                         __threadfence_block();
                         if (vload(sh.committed) < com + kRS - 1) {
                             c0 = com;
+                            acc0 = acc_seen;
                             go = 1;
                             if (rd) {
                                 vstore(redo[team], 0);
@@ -1103,11 +1153,12 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                     __nanosleep(16);
                 }
                 if (go == 1) {
-                    Slot &S = sh.slots[mm % kRS];
+                    Slot &S = sh.slots[(mm) & (kRS - 1)];
                     S.self_slot = -1;
                     S.has_last = 0;
                     S.arrive = 0;
                     S.c0 = c0;
+                    S.acc0 = acc0;
                     __threadfence_block();
                     vstore(S.tag, mm + 1);
                 }
@@ -1115,6 +1166,7 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 tc.m[p] = mm;
                 tc.c0[p] = c0;
                 __threadfence_block();
+                cyc_idle += clock64() - ti;
             }
             __syncwarp();
             if (j == 0) {
@@ -1133,11 +1185,10 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                         const WordRec &Wk = C.words(k);
                         const uint32_t w0 = Wk.w[0];
                         const int ty = (w0 < a.thr_disp) ? 0 : ((w0 < a.thr_ins) ? 1 : 2);
-                        const Slot &Sk = sh.slots[k % kRS];
-                        if (ty != 0 && vload(Sk.tag) == k + 1 && vload(Sk.arrive) == G && Sk.t.possible) {
+                        const Slot &Sk = sh.slots[(k) & (kRS - 1)];
+                        if (ty != 0 && vload(Sk.tag) == k + 1 && vload(Sk.arrive) == G + 1 && Sk.t.possible) {
                             sk = Sk.t.s;
-                            float dU = 0.f;
-                            for (int q = 0; q < G; ++q) dU += F32 ? Sk.ph[q] : (float)Sk.pd[q];
+                            const float dU = F32 ? Sk.th : (float)Sk.td;
                             const float lnK = (ty == 1) ? a.lnzv_f[sk] - sh.ln_n1[sk] : sh.ln_n[sk] - a.lnzv_f[sk];
                             if (Wk.lnu < lnK - (float)a.beta * dU) d = (ty == 1) ? 1 : -1;
                         } else if (ty != 0 && vload(sh.likely[ty - 1])) {
@@ -1157,16 +1208,25 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             // barrier counts warps, not lanes
             __syncwarp();
             team_sync(1 + team, G * 32);
-            if (tc.go[p] == 2) break;
+            if (tc.go[p] == 2) {
+                if (j == 0 && lane == 0) {
+                    atomicAdd(&team_cyc[0], cyc_idle);
+                    atomicAdd(&team_cyc[1], cyc_eval);
+                    atomicAdd(&team_cyc[2], n_eval);
+                }
+                break;
+            }
+            const unsigned long long te = clock64();
             const int m = tc.m[p];
             const Trial t = C.make_trial(m, tc.ns[p]);
-            Slot &S = sh.slots[m % kRS];
+            Slot &S = sh.slots[(m) & (kRS - 1)];
             const typename Chain<F32, VIR>::Part P = C.template eval_part<F32, KU>(t, j, G);
             if (P.self_slot >= 0) S.self_slot = P.self_slot;
             if (P.has_last) {
                 S.last_val = P.last;
                 S.has_last = 1;
             }
+            if (j == 0 && lane < a.S) S.nsu[lane] = tc.ns[p][lane];
             if (lane == 0) {
                 if (j == 0) S.t = t;
                 S.pseq[j] = P.seq;
@@ -1182,16 +1242,72 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 }
             }
             __syncwarp();
+            int last = 0;
             if (lane == 0) {
                 __threadfence_block();
-                atomicAdd(&S.arrive, 1);
+                last = atomicAdd(&S.arrive, 1) == G - 1;
+                if (j == 0) {
+                    cyc_eval += clock64() - te;
+                    ++n_eval;
+                }
+            }
+            // the team's last warp adds the G partial sums in a fixed order
+            // (lanes 0 .. G-1, butterfly) and marks the move arrive = G + 1:
+            // the committer reads one total
+            if (__shfl_sync(0xffffffffu, last, 0)) {
+                __threadfence_block();
+                if constexpr (F32) {
+                    const volatile Slot &V = S;
+                    FF v = {lane < G ? V.ph[lane] : 0.f, lane < G ? V.pl[lane] : 0.f};
+                    float u = lane < G ? V.pu[lane] : 0.f;
+                    float w = (VIR && lane < G) ? V.pw[lane] : 0.f;
+#pragma unroll
+                    for (int o = kGMax / 2; o > 0; o >>= 1) {
+                        FF x;
+                        x.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+                        x.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+                        v = ff_add(v, x);
+                        u += __shfl_xor_sync(0xffffffffu, u, o);
+                        w += __shfl_xor_sync(0xffffffffu, w, o);
+                    }
+                    if (lane == 0) {
+                        S.th = v.hi;
+                        S.tl = v.lo;
+                        S.tu = u;
+                        S.tw = w;
+                    }
+                } else {
+                    const volatile Slot &V = S;
+                    double v = lane < G ? V.pd[lane] : 0.0, u = lane < G ? V.pa[lane] : 0.0;
+                    double w = (VIR && lane < G) ? V.pwd[lane] : 0.0;
+#pragma unroll
+                    for (int o = kGMax / 2; o > 0; o >>= 1) {
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                        u += __shfl_xor_sync(0xffffffffu, u, o);
+                        w += __shfl_xor_sync(0xffffffffu, w, o);
+                    }
+                    if (lane == 0) {
+                        S.td = v;
+                        S.ta = u;
+                        S.tdw = w;
+                    }
+                }
+                if (lane == 0) {
+                    __threadfence_block();
+                    atomicAdd(&S.arrive, 1);
+                }
+                __syncwarp();
             }
         }
     } else if (warp == 0) {
         // ------------------------------------------------------------ committer
         int att_id[2] = {0, 0}, acc_id[2] = {0, 0};  // insertions, deletions (lane 0)
+        unsigned long long cw = 0, cv = 0, cd = 0, ca = 0, ct = 0;  // committer cycles (see ChainOut::prof)
+        unsigned long long cv_e = 0, cv_l = 0, cv_p = 0, cb = 0;
+        int nacc = 0;  // moves accepted so far (the committer's count, published in sh.nacc)
         for (int m = 0; m < n; ++m) {
-            Slot &S = sh.slots[m % kRS];
+            const unsigned long long tm0 = clock64();
+            Slot &S = sh.slots[(m) & (kRS - 1)];
             const int team = m % NTEAM;
             bool ok = true;
             if (m == a.stall_at) {
@@ -1214,15 +1330,17 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 if (!ok) break;
             }
             int c0 = 0, attempt = 0;
+            Trial tcur;
             for (;; ++attempt) {
                 // wait for the evaluation of m and for room in the keeper's book
+                const unsigned long long tw = clock64();
                 Wait wt;
                 for (;;) {
                     int r = 0;
                     if (lane == 0) {
                         const int tg = vload(S.tag);
                         __threadfence_block();
-                        r = tg == m + 1 && vload(S.arrive) == G && m < vload(sh.booked) + kRS;
+                        r = tg == m + 1 && vload(S.arrive) == G + 1 && m < vload(sh.booked) + kRS;
                     }
                     r = __shfl_sync(0xffffffffu, r, 0);
                     if (r) break;
@@ -1236,13 +1354,33 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                     }
                 }
                 if (!ok) break;
+                const unsigned long long tv = clock64();
+                cw += tv - tw;
                 __threadfence_block();
                 c0 = S.c0;
+                tcur = S.t;  // one copy in registers for the checks and the decision
                 // the team's warps must have read the counts of one epoch
                 // (their item ranges follow the counts)
+                // no move accepted since the evaluation started: nothing it
+                // read has changed (counts, records, cells), only the pick
+                // is left to check
+                const bool quiet = S.acc0 == nacc;
                 const int q0 = S.pseq[0];
-                const bool one_epoch = __all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0;
-                if (c0 == m || (one_epoch && still_valid<F32>(C, sh, S.t, c0, m, T, lane))) break;
+                const bool one_epoch = quiet || (__all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0);
+                const unsigned long long tv1 = clock64();
+                bool valid = c0 == m || quiet || (one_epoch && logs_ok(C, sh, tcur, c0, m, lane));
+                const unsigned long long tv2 = clock64();
+                // the counts at the move's turn equal those the evaluation
+                // picked with: the same particle (else compare the picks)
+                const bool same_counts =
+                    __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == sh.ns_ring[m & (kRS - 1)][lane]);
+                valid = valid && (c0 == m || same_counts || pick_ok(C, sh, tcur, m));
+                const unsigned long long tv3 = clock64();
+                cv += tv3 - tv;
+                cv_e += tv1 - tv;
+                cv_l += tv2 - tv1;
+                cv_p += tv3 - tv2;
+                if (valid) break;
                 // evaluate again against the configuration after m moves
                 if (lane == 0) {
                     vstore(S.tag, 0);
@@ -1252,44 +1390,23 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 __syncwarp();
             }
             if (!ok) break;
-            const Trial t = S.t;
+            const unsigned long long td = clock64();
+            const Trial t = tcur;
             const int self_slot = S.self_slot;
             const uint4 last_val = S.last_val;
-            // the team's partial sums in a fixed order (lanes >= G add zeros);
-            // lanes 0 .. 7 hold the totals and every lane takes lane 0's, so
-            // the whole warp decides alike
+            // the team's totals (summed by its last warp in a fixed order)
             FF e = {0.f, 0.f};
             float uab = 0.f;
             double de = 0.0, da = 0.0, dW = 0.0;
             if constexpr (F32) {
-                FF v = {lane < G ? S.ph[lane] : 0.f, lane < G ? S.pl[lane] : 0.f};
-                float u = lane < G ? S.pu[lane] : 0.f;
-                float w = (VIR && lane < G) ? S.pw[lane] : 0.f;
-#pragma unroll
-                for (int o = kGMax / 2; o > 0; o >>= 1) {
-                    FF x;
-                    x.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-                    x.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-                    v = ff_add(v, x);
-                    u += __shfl_xor_sync(0xffffffffu, u, o);
-                    w += __shfl_xor_sync(0xffffffffu, w, o);
-                }
-                e.hi = __shfl_sync(0xffffffffu, v.hi, 0);
-                e.lo = __shfl_sync(0xffffffffu, v.lo, 0);
-                uab = __shfl_sync(0xffffffffu, u, 0);
-                dW = (double)__shfl_sync(0xffffffffu, w, 0);
+                e.hi = S.th;
+                e.lo = S.tl;
+                uab = S.tu;
+                dW = (double)S.tw;
             } else {
-                double v = lane < G ? S.pd[lane] : 0.0, u = lane < G ? S.pa[lane] : 0.0;
-                double w = (VIR && lane < G) ? S.pwd[lane] : 0.0;
-#pragma unroll
-                for (int o = kGMax / 2; o > 0; o >>= 1) {
-                    v += __shfl_xor_sync(0xffffffffu, v, o);
-                    u += __shfl_xor_sync(0xffffffffu, u, o);
-                    w += __shfl_xor_sync(0xffffffffu, w, o);
-                }
-                de = __shfl_sync(0xffffffffu, v, 0);
-                da = __shfl_sync(0xffffffffu, u, 0);
-                dW = __shfl_sync(0xffffffffu, w, 0);
+                de = S.td;
+                da = S.ta;
+                dW = S.tdw;
                 e.hi = __double2float_rn(de);
                 uab = __double2float_rn(da);
             }
@@ -1297,7 +1414,8 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             const int type = t.type, sp = t.s;
             const long long ns = sh.n[sp];
             // the Metropolis test in FP32 with an error band
-            const int dec = t.possible ? decide_f32(a, type, sp, (int)ns, C.words(m).lnu, e.hi + e.lo, uab) : 0;
+            const int dec = t.possible ? decide_f32(a, type, sp, sh.ln_n[sp], sh.ln_n1[sp], C.words(m).lnu, e.hi + e.lo, uab)
+                                       : 0;
             int fin = dec == 1 ? 1 : 0, use64 = F32 ? 0 : 1;
             double lnA_d = 0.0;
             if (dec < 0) {
@@ -1341,14 +1459,18 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 }
                 break;
             }
-            LogRec &L = sh.logs[m % kRS];
+            LogRec &L = sh.logs[(m) & (kRS - 1)];
+            const unsigned long long tapp = clock64();
+            cd += tapp - td;
             if (fin & 1) C.apply(t, self_slot, last_val, L);
-            else if (lane == 0) L.flags = 0;
+            else if (lane == 0) L.head.x = 0;
+            const unsigned long long tb0 = clock64();
+            ca += tb0 - tapp;
             __syncwarp();
-            if (lane < kMaxSpecies) sh.ns_ring[(m + 1) % kRS][lane] = (int)sh.n[lane];
+            if (lane < kMaxSpecies) sh.ns_ring[((m + 1)) & (kRS - 1)][lane] = (int)sh.n[lane];
             __syncwarp();
             if (lane == 0) {
-                BookRec &B = sh.book[m % kRS];
+                BookRec &B = sh.book[(m) & (kRS - 1)];
                 B.dU64 = de;
                 B.dW = dW;
                 B.hi = e.hi;
@@ -1363,13 +1485,32 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
                 B.possible = t.possible;
                 B.refined = refined;
                 B.ns = ns;
+                // the move's writes are visible before the accepted count and
+                // the commit count say so
                 __threadfence_block();
+                if (fin & 1) vstore(sh.nacc, nacc + 1);
                 vstore(B.ready, m + 1);
                 vstore(sh.committed, m + 1);
             }
+            nacc += fin & 1;
             __syncwarp();
+            const unsigned long long tend = clock64();
+            cb += tend - tb0;
+            ct += tend - tm0;
         }
-        if (lane == 0) vstore(sh.stop, 1);  // evaluators and keeper wind down
+        if (lane == 0) {
+            vstore(sh.stop, 1);  // evaluators and keeper wind down
+            ChainOut &o = *a.out;
+            o.prof[0] = cw;
+            o.prof[1] = cv;
+            o.prof[2] = cd;
+            o.prof[3] = ca;
+            o.prof[4] = ct;
+            o.prof[8] = cv_e;
+            o.prof[9] = cv_l;
+            o.prof[10] = cv_p;
+            o.prof[11] = cb;
+        }
     } else if (warp == keeper_warp) {
         // ------------------------------------------------------------ keeper
         double E = *a.d_energy, sumE = 0.0;
@@ -1402,12 +1543,12 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
             }
             // book the committed moves in order
             int rdy = 0;
-            if (lane == 0 && mb < n) rdy = vload(sh.book[mb % kRS].ready);
+            if (lane == 0 && mb < n) rdy = vload(sh.book[(mb) & (kRS - 1)].ready);
             rdy = __shfl_sync(0xffffffffu, rdy, 0);
             if (mb < n && rdy == mb + 1) {
                 __threadfence_block();
                 if (lane == 0) {
-                    const BookRec &B = sh.book[mb % kRS];
+                    const BookRec &B = sh.book[(mb) & (kRS - 1)];
                     const int type = B.type;
                     att0 += type == 0;
                     att1 += type == 1;
@@ -1507,6 +1648,9 @@ __global__ void __launch_bounds__((G * NTEAM + 2) * 32, 1) k_chain(const ChainAr
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
         o.t0 = t_start;
         o.t1 = t_end;
+        o.prof[5] = team_cyc[0];
+        o.prof[6] = team_cyc[1];
+        o.prof[7] = team_cyc[2];
     }
 }
 
@@ -1529,7 +1673,7 @@ static void *chain_kernel(int config)
     }
 }
 
-int chain_threads(int config) { return (kConfigG[config] * kConfigT[config] + 2) * 32; }
+int chain_threads(int) { return kChainWarps * 32; }
 
 // One chain of a launch: its context, random stream, moves and outputs.
 struct ChainJob {
@@ -1766,6 +1910,7 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
             ctx->order_valid = false;
             ctx->last_refetch += o.reevaluated;
             ctx->last_refines += o.refines;
+            for (int q = 0; q < 12; ++q) ctx->last_prof[q] += (double)o.prof[q];
             j.done += o.moves_done;
             if (o.status & kStatusNonFinite) j.result = GCMC_ERR_NONFINITE;
             if (o.status & kStatusTimeout) {
@@ -1904,6 +2049,7 @@ gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_mo
     j.agg.sum_virial = vir ? 0.0 : NAN;
     ctx->last_refetch = 0;
     ctx->last_refines = 0;
+    for (double &v : ctx->last_prof) v = 0.0;
     std::string err;
     st = run_jobs_tuned(jobs, ctx->stream, ctx->precision == GCMC_FP32, ctx->chain_config, bufs, &ctx->launches,
                         &err, false, nullptr);
@@ -1975,6 +2121,7 @@ gcmc_status run_batch(gcmc_ctx *const *ctxs, int K, const uint64_t *seeds, uint6
         j.agg.sum_virial = vir ? 0.0 : NAN;
         ctxs[k]->last_refetch = 0;
         ctxs[k]->last_refines = 0;
+        for (double &v : ctxs[k]->last_prof) v = 0.0;
     }
     gcmc_status st = run_jobs_tuned(jobs, stream, f32, config, bufs, launches, err, use_graph && stream != nullptr,
                                     probe_ms, dev_ms);

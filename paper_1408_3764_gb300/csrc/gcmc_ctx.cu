@@ -593,6 +593,13 @@ gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refi
     return GCMC_OK;
 }
 
+gcmc_status gcmc_chain_profile(gcmc_ctx *ctx, double *cycles)
+{
+    if (!ctx || !cycles) return GCMC_ERR_INVALID_ARG;
+    for (int q = 0; q < 12; ++q) cycles[q] = ctx->last_prof[q];
+    return GCMC_OK;
+}
+
 const char *gcmc_last_error(gcmc_ctx *ctx)
 {
     if (!ctx) return "null context";

@@ -65,6 +65,7 @@ struct gcmc_ctx {
     int64_t launches = 0;  // kernels this context has launched
     int64_t last_refetch = 0;  // chain moves whose prefetched data was re-fetched (last run)
     int64_t last_refines = 0;
+    double last_prof[12] = {};  // chain kernel cycle counters of the last run (ChainOut::prof)
     int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)
     uint64_t wait_ns = 0;   // limit of the chain kernel's waits (0: the default, 1 s)
     int64_t stall_at = -1;  // diagnostic stall of the committer at this move of a call (-1 none)

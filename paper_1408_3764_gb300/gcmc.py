@@ -162,6 +162,16 @@ class Box:
                                             out[1:].ctypes.data_as(C.c_void_p)), self._h)
         return dict(refetched=int(out[0]), refined=int(out[1]))
 
+    def chain_profile(self) -> dict:
+        """SM cycles of the last chain run by role: committer waiting, validity, decision,
+        applying, loop total; team leaders idle, teams evaluating, evaluations."""
+        out = np.zeros(12, np.float64)
+        check(self._lib.gcmc_chain_profile(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
+        keys = ("commit_wait", "commit_valid", "commit_decide", "commit_apply", "commit_total",
+                "leader_idle", "team_eval", "evaluations", "valid_epoch", "valid_logs", "valid_pick",
+                "commit_book")
+        return dict(zip(keys, out.tolist()))
+
     def counts(self) -> np.ndarray:
         """Particles per species."""
         out = np.zeros(MAX_SPECIES, np.int64)

@@ -155,6 +155,16 @@ gcmc_status gcmc_destroy(gcmc_ctx *ctx);
  * CUDA. */
 gcmc_status gcmc_build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
 
+/* The current configuration as input for gcmc_build_cells: pos (device,
+ * N x 3 FP64) receives each particle's coordinates (the centre of its grid
+ * point, which quantises back to the same point) and species (device, N
+ * int32) its species, in species-major order (species 0 by index, then
+ * species 1, ...), so that building from them reproduces the configuration
+ * with the same particle ids.  n (host, may be NULL) receives N.  Launches
+ * one kernel on the context's stream; nothing waits.
+ * Errors: STATE (no cells), INVALID_ARG (NULL arrays while N > 0), CUDA. */
+gcmc_status gcmc_export_positions(gcmc_ctx *ctx, double *pos, int32_t *species, int64_t *n);
+
 /* The compact cell list of the last gcmc_build_cells: cell_start and
  * cell_count (device, n_cells int32 each) and order (device, n int32: input
  * indices sorted by cell, input order within a cell).  Any pointer may be
@@ -378,6 +388,23 @@ gcmc_status gcmc_batch_destroy(gcmc_batch *batch);
  * failing chain's status (its context has the message); INVALID_ARG. */
 gcmc_status gcmc_batch_run_moves(gcmc_batch *batch, const uint64_t *seeds, uint64_t first_move, int64_t n_moves,
                                  const gcmc_move_mix *mixes, gcmc_move_stats *stats);
+
+/* gcmc_build_cells and gcmc_total_energy for every chain of the batch, the
+ * work of all contexts issued on their own streams with two host
+ * synchronisations in all (the per-context calls synchronise six times
+ * each).  pos, species: host arrays of n_chains device pointers (FP64 N x 3,
+ * int32 N); n: host, n_chains counts; energies: host, n_chains doubles, or
+ * NULL.  Errors: as gcmc_build_cells and gcmc_total_energy, the first
+ * failing chain's (gcmc_batch_last_error names it). */
+gcmc_status gcmc_batch_prepare(gcmc_batch *batch, const double *const *pos, const int32_t *const *species,
+                               const int64_t *n, double *energies);
+
+/* gcmc_energy_grad for every chain (forces, energy and virial; no table
+ * derivatives), one host synchronisation in all.  dpos: host array of
+ * n_chains device pointers (FP32 N x 3, species-major) or NULL entries, or
+ * dpos = NULL; energies, virials: host, n_chains doubles, or NULL.
+ * Errors: as gcmc_energy_grad, the first failing chain's. */
+gcmc_status gcmc_batch_energy_grad(gcmc_batch *batch, float *const *dpos, double *energies, double *virials);
 
 /* Per-chain move records for the following gcmc_batch_run_moves calls:
  * traces is a host array of n_chains device pointers, each NULL or room for

@@ -40,6 +40,21 @@ typedef struct {
  * Errors: INVALID_ARG, CUDA. */
 gcmc_status gcmc_probe_latency(void *stream, int64_t working_set_bytes, gcmc_probe_result *out);
 
+/* Measured throughput of the arithmetic pipes on the current device (the
+ * denominators of the FP32/FP64-bound rooflines): every thread of 8 CTAs of
+ * 256 threads per SM runs 8 independent dependent chains.  fp32_tflops and
+ * fp64_tflops count an FMA as 2 operations; mufu_gops counts approximate
+ * reciprocals of the special-function unit; sms is the device's SM count.
+ * Allocates and frees 16 bytes.  out: host.  Errors: INVALID_ARG, CUDA. */
+typedef struct {
+    double fp32_tflops;
+    double fp64_tflops;
+    double mufu_gops;
+    int32_t sms;
+    int32_t reserved;
+} gcmc_pipe_peaks;
+gcmc_status gcmc_probe_pipes(void *stream, gcmc_pipe_peaks *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,11 @@ class ProbeResult(C.Structure):
     _fields_ = [("l2_hop_ns", C.c_double), ("sync_round_ns", C.c_double), ("philox_ns", C.c_double),
                 ("log_ns", C.c_double), ("floor_ns", C.c_double), ("working_set_bytes", C.c_int64)]
 
+class PipePeaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double), ("mufu_gops", C.c_double),
+                ("sms", C.c_int32), ("reserved", C.c_int32)]
+
+
 # every symbol include/gcmc.h declares, with (restype, argtypes)
 _vp = C.c_void_p
 SIGNATURES = {
@@ -64,6 +69,7 @@ SIGNATURES = {
     "gcmc_destroy": (C.c_int, [_vp]),
     "gcmc_build_cells": (C.c_int, [_vp, _vp, _vp, C.c_int64]),
     "gcmc_cell_list": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gcmc_export_positions": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gcmc_trial_energy": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
     "gcmc_run_moves": (C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_int64, C.POINTER(MoveMix),
                                  C.POINTER(MoveStats), _vp]),
@@ -89,6 +95,8 @@ SIGNATURES = {
     "gcmc_batch_destroy": (C.c_int, [_vp]),
     "gcmc_batch_run_moves": (C.c_int, [_vp, _vp, C.c_uint64, C.c_int64, _vp, _vp]),
     "gcmc_batch_set_traces": (C.c_int, [_vp, _vp]),
+    "gcmc_batch_prepare": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gcmc_batch_energy_grad": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gcmc_batch_config": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "gcmc_batch_launches": (C.c_int, [_vp, _vp]),
     "gcmc_batch_device_ms": (C.c_int, [_vp, C.POINTER(C.c_double)]),
@@ -96,6 +104,7 @@ SIGNATURES = {
     "gcmc_last_error": (C.c_char_p, [_vp]),
     "gcmc_version": (C.c_char_p, []),
     "gcmc_probe_latency": (C.c_int, [_vp, C.c_int64, C.POINTER(ProbeResult)]),
+    "gcmc_probe_pipes": (C.c_int, [_vp, C.POINTER(PipePeaks)]),
 }
 
 _lib = None

@@ -11,6 +11,7 @@
 //                      writes the compact and padded cell-major layouts
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "gcmc_ctx.h"
 
@@ -274,7 +275,10 @@ static unsigned grid_for(gcmc_ctx *ctx, int64_t work, int block)
     return (unsigned)b;
 }
 
-gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n)
+// Phase one of a build: quantise, count, rank within species and scan the
+// cell counts, all on the context's stream; the counts and the status bits
+// the sizes depend on are copied to pinned host memory.  Nothing waits.
+gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n)
 {
     cudaStream_t st = ctx->stream;
     const int S = ctx->S;
@@ -325,11 +329,50 @@ gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species
     }
     gcmc_status s1 = exclusive_scan(ctx, ctx->cell_count, ncell, ctx->cell_start, part, vmax);
     if (s1 != GCMC_OK) return s1;
-    int64_t hsmall[9] = {0};
+    s1 = ensure_pinned(ctx, kPinnedBytes);
+    if (s1 != GCMC_OK) return s1;
+    int64_t *hp = (int64_t *)ctx->h_pinned;
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp, small, 9 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp + 9, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ctx->pend_n = n;
+    ctx->pend_off[0] = o_grid;
+    ctx->pend_off[1] = o_cell;
+    ctx->pend_off[2] = o_sidx;
+    ctx->pend_off[3] = o_tmp;
+    ctx->pend_off[4] = o_fill;
+    ctx->pend_off[5] = o_small;
+    ctx->built = false;
+    ctx->compact_valid = false;
+    ctx->order_valid = false;
+    ctx->energy_valid = false;
+    ctx->virial_valid = false;
+    ctx->mc_valid = false;
+    return GCMC_OK;
+}
+
+// Phase two, once the stream has passed phase one: checks the input, sizes
+// (and if needed grows) the configuration arrays, places and orders the
+// particles.  Launches only; nothing waits.
+gcmc_status build_finish(gcmc_ctx *ctx)
+{
+    cudaStream_t st = ctx->stream;
+    const int S = ctx->S;
+    const int64_t ncell = ctx->ncell;
+    const int64_t n = ctx->pend_n;
+    if (n < 0) return fail(ctx, GCMC_ERR_STATE, "gcmc_build_cells: no build under way");
+    ctx->pend_n = -1;
+    char *base = (char *)ctx->scratch;
+    uint4 *grid = (uint4 *)(base + ctx->pend_off[0]);
+    int32_t *cellid = (int32_t *)(base + ctx->pend_off[1]);
+    int32_t *sidx = (int32_t *)(base + ctx->pend_off[2]);
+    int32_t *tmp = (int32_t *)(base + ctx->pend_off[3]);
+    int32_t *fill = (int32_t *)(base + ctx->pend_off[4]);
+    int64_t *small = (int64_t *)(base + ctx->pend_off[5]);
+    (void)grid;
+    int64_t hsmall[9];
+    memcpy(hsmall, ctx->h_pinned, sizeof(hsmall));
     int hstatus = 0;
-    GCMC_CUDA(ctx, cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, st));
-    GCMC_CUDA(ctx, cudaMemcpyAsync(&hstatus, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GCMC_CUDA(ctx, cudaStreamSynchronize(st));
+    memcpy(&hstatus, (int64_t *)ctx->h_pinned + 9, sizeof(int));
     ctx->built = false;
     ctx->compact_valid = false;
     ctx->order_valid = false;
@@ -390,6 +433,14 @@ gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species
     ctx->compact_valid = true;
     ctx->order_valid = true;
     return GCMC_OK;
+}
+
+gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n)
+{
+    gcmc_status st = build_begin(ctx, pos, species, n);
+    if (st != GCMC_OK) return st;
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return build_finish(ctx);
 }
 
 gcmc_status make_compact(gcmc_ctx *ctx)

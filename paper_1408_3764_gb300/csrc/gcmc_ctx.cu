@@ -194,6 +194,17 @@ gcmc_status gcmc_build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *sp
     return build_cells(ctx, pos, species, n);
 }
 
+gcmc_status gcmc_export_positions(gcmc_ctx *ctx, double *pos, int32_t *species, int64_t *n)
+{
+    if (!ctx) return GCMC_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, GCMC_ERR_STATE, "gcmc_export_positions: cells not built");
+    int64_t N = 0;
+    for (int s = 0; s < ctx->S; ++s) N += ctx->n_host[s];
+    if (n) *n = N;
+    if (N > 0 && (!pos || !species)) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_export_positions: NULL arrays");
+    return export_positions(ctx, pos, species);
+}
+
 gcmc_status gcmc_cell_list(gcmc_ctx *ctx, int32_t *cell_start, int32_t *cell_count, int32_t *order)
 {
     if (!ctx) return GCMC_ERR_INVALID_ARG;
@@ -683,6 +694,69 @@ gcmc_status gcmc_batch_run_moves(gcmc_batch *b, const uint64_t *seeds, uint64_t 
                                b->traces.empty() ? nullptr : b->traces.data());
     if (st != GCMC_OK) b->err = err.empty() ? "gcmc_batch_run_moves: a chain failed (see its context)" : err;
     return st;
+}
+
+// A failing chain's status, with its message in the batch.
+static gcmc_status batch_fail(gcmc_batch *b, int k, gcmc_status st)
+{
+    b->err = "chain " + std::to_string(k) + ": " + b->ctxs[k]->err;
+    return st;
+}
+
+static gcmc_status batch_sync(gcmc_batch *b)
+{
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        const cudaError_t e = cudaStreamSynchronize(b->ctxs[k]->stream);
+        if (e != cudaSuccess) return batch_fail(b, (int)k, cuda_fail(b->ctxs[k], e, "cudaStreamSynchronize"));
+    }
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_prepare(gcmc_batch *b, const double *const *pos, const int32_t *const *species,
+                               const int64_t *n, double *energies)
+{
+    if (!b) return GCMC_ERR_INVALID_ARG;
+    const int K = (int)b->ctxs.size();
+    if (!pos || !species || !n) {
+        b->err = "gcmc_batch_prepare: NULL arrays";
+        return GCMC_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < K; ++k) {
+        if (n[k] < 0 || n[k] > (int64_t)kMaxSpecies * (1ll << 24) || (n[k] > 0 && (!pos[k] || !species[k]))) {
+            b->err = "gcmc_batch_prepare: bad n or NULL arrays of chain " + std::to_string(k);
+            return GCMC_ERR_INVALID_ARG;
+        }
+    }
+    gcmc_status st;
+    for (int k = 0; k < K; ++k)
+        if ((st = build_begin(b->ctxs[k], pos[k], species[k], n[k])) != GCMC_OK) return batch_fail(b, k, st);
+    if ((st = batch_sync(b)) != GCMC_OK) return st;
+    for (int k = 0; k < K; ++k) {
+        if ((st = build_finish(b->ctxs[k])) != GCMC_OK) return batch_fail(b, k, st);
+        if ((st = total_energy_begin(b->ctxs[k])) != GCMC_OK) return batch_fail(b, k, st);
+    }
+    if ((st = batch_sync(b)) != GCMC_OK) return st;
+    for (int k = 0; k < K; ++k)
+        if ((st = total_energy_finish(b->ctxs[k], energies ? energies + k : nullptr)) != GCMC_OK)
+            return batch_fail(b, k, st);
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_energy_grad(gcmc_batch *b, float *const *dpos, double *energies, double *virials)
+{
+    if (!b) return GCMC_ERR_INVALID_ARG;
+    const int K = (int)b->ctxs.size();
+    gcmc_status st;
+    for (int k = 0; k < K; ++k) {
+        if (!b->ctxs[k]->built) return batch_fail(b, k, fail(b->ctxs[k], GCMC_ERR_STATE, "cells not built"));
+        if ((st = energy_grad_begin(b->ctxs[k], dpos ? dpos[k] : nullptr)) != GCMC_OK) return batch_fail(b, k, st);
+    }
+    if ((st = batch_sync(b)) != GCMC_OK) return st;
+    for (int k = 0; k < K; ++k)
+        if ((st = energy_grad_finish(b->ctxs[k], nullptr, nullptr, energies ? energies + k : nullptr,
+                                     virials ? virials + k : nullptr)) != GCMC_OK)
+            return batch_fail(b, k, st);
+    return GCMC_OK;
 }
 
 gcmc_status gcmc_batch_set_traces(gcmc_batch *b, gcmc_trace *const *traces)

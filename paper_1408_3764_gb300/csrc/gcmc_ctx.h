@@ -57,6 +57,8 @@ struct gcmc_ctx {
     size_t d_red_len = 0;
     void *h_pinned = nullptr;       // small pinned host staging
     size_t h_pinned_bytes = 0;
+    int64_t pend_n = -1;            // a build between its two phases: its particle count
+    size_t pend_off[6] = {};        // and its scratch layout
 
     double energy = 0.0;
     bool energy_valid = false;
@@ -94,6 +96,12 @@ gcmc_status cuda_fail(gcmc_ctx *ctx, cudaError_t e, const char *where);
         if (e_ != cudaSuccess) return gcmc::cuda_fail(ctx, e_, #call); \
     } while (0)
 
+// Pinned host words that builds and energy calls read back (per context),
+// in 8-byte words: [0 .. 7] species totals, [8] largest cell count, [9]
+// status bits of a build; [10] energy, [11] virial, [12] status of the
+// full-system energy; [16 ..] the gradient's scalars, then its status.
+constexpr size_t kPinnedBytes = 8 * (16 + 2 + 2 * kMaxSpecies * kMaxSpecies + 8);
+
 gcmc_status ensure_scratch(gcmc_ctx *ctx, size_t bytes);
 gcmc_status ensure_red(gcmc_ctx *ctx, size_t n);
 gcmc_status ensure_pinned(gcmc_ctx *ctx, size_t bytes);
@@ -101,6 +109,11 @@ gcmc_status read_status(gcmc_ctx *ctx, int *bits);
 
 // cells.cu
 gcmc_status build_cells(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
+// The two phases of build_cells (the stream must pass phase one before
+// phase two runs on the host): the batched calls begin every box's build,
+// wait once, and finish them all.
+gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species, int64_t n);
+gcmc_status build_finish(gcmc_ctx *ctx);
 gcmc_status make_compact(gcmc_ctx *ctx);
 gcmc_status relayout(gcmc_ctx *ctx, int new_cap, int64_t new_maxN);
 // out[i] = exclusive prefix sum of in[0 .. n), out[n] = the total; part:
@@ -114,9 +127,18 @@ gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *specie
 // running values; with virial_only the running energy is left as it is and
 // only the virial is set.
 gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only = false);
+// total_energy in two phases: launch (the sums are copied to pinned host
+// memory) and, after the stream has passed them, read.
+gcmc_status total_energy_begin(gcmc_ctx *ctx, bool virial_only = false);
+gcmc_status total_energy_finish(gcmc_ctx *ctx, double *energy, bool virial_only = false);
 gcmc_status total_energy_noalloc(gcmc_ctx *ctx, double *energy_dev);
 gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
                         double *virial);
+gcmc_status energy_grad_begin(gcmc_ctx *ctx, float *dpos);
+gcmc_status energy_grad_finish(gcmc_ctx *ctx, double *deps, double *dsigma, double *energy, double *virial);
+// Writes the configuration as real coordinates (the centres of the grid
+// points, which quantise back to them) and species, species-major.
+gcmc_status export_positions(gcmc_ctx *ctx, double *pos, int32_t *species);
 
 // chain.cu
 gcmc_status run_moves(gcmc_ctx *ctx, uint64_t seed, uint64_t first, int64_t n_moves,

@@ -13,6 +13,7 @@
 // FP64 mode: everything in FP64.  k_cell_energy_padded (allocation-free
 // energy) keeps plain FP32 pair terms and per-lane sums in FP32 mode.
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -826,11 +827,13 @@ gcmc_status trial_energy(gcmc_ctx *ctx, const double *pos, const int32_t *specie
     return GCMC_OK;
 }
 
-gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
+gcmc_status total_energy_begin(gcmc_ctx *ctx, bool virial_only)
 {
     gcmc_status st = make_compact(ctx);
     if (st != GCMC_OK) return st;
     st = ensure_red(ctx, 2 * (size_t)ctx->ncell + 8);
+    if (st != GCMC_OK) return st;
+    st = ensure_pinned(ctx, kPinnedBytes);
     if (st != GCMC_OK) return st;
     float r2lo, r2hi;
     bool wrap;
@@ -853,40 +856,55 @@ gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
     k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 2, ctx->d_red + 2 * ctx->ncell);
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());
-    double ew[3] = {0.0, 0.0, 0.0};
-    GCMC_CUDA(ctx, cudaMemcpyAsync(ew, ctx->d_red + 2 * ctx->ncell, 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                                   ctx->stream));
-    int bits = 0;
-    GCMC_CUDA(ctx, cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (bits & kStatusTimeout)
-        return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_total_energy: a bulk copy did not complete within the wait limit");
-    const double e = ew[0];
-    ctx->virial = ew[1];
-    ctx->virial_valid = true;
-    // the running values on the device come from the device (no second host round trip)
+    double *hp = (double *)ctx->h_pinned;
     const double *dsum = ctx->d_red + 2 * ctx->ncell;
-    if (virial_only) {
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp + 10, dsum, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp + 12, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    // the running values on the device come from the device (no second host round trip)
+    if (virial_only)
         GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy + 1, dsum + 1, sizeof(double), cudaMemcpyDeviceToDevice,
                                        ctx->stream));
-    } else {
-        ctx->energy = e;
-        ctx->energy_valid = true;
+    else
         GCMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_energy, dsum, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
                                        ctx->stream));
+    return GCMC_OK;
+}
+
+gcmc_status total_energy_finish(gcmc_ctx *ctx, double *energy, bool virial_only)
+{
+    const double *hp = (const double *)ctx->h_pinned;
+    int bits = 0;
+    memcpy(&bits, hp + 12, sizeof(int));
+    if (bits & kStatusTimeout)
+        return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_total_energy: a bulk copy did not complete within the wait limit");
+    const double e = hp[10];
+    ctx->virial = hp[11];
+    ctx->virial_valid = true;
+    if (!virial_only) {
+        ctx->energy = e;
+        ctx->energy_valid = true;
     }
     if (energy) *energy = e;
     return GCMC_OK;
 }
 
-gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
-                        double *virial)
+gcmc_status total_energy(gcmc_ctx *ctx, double *energy, bool virial_only)
+{
+    gcmc_status st = total_energy_begin(ctx, virial_only);
+    if (st != GCMC_OK) return st;
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return total_energy_finish(ctx, energy, virial_only);
+}
+
+gcmc_status energy_grad_begin(gcmc_ctx *ctx, float *dpos)
 {
     gcmc_status st = make_compact(ctx);
     if (st != GCMC_OK) return st;
     const int S = ctx->S;
     const int width = 2 + 2 * S * S;
     st = ensure_red(ctx, (size_t)ctx->ncell * width + width);
+    if (st != GCMC_OK) return st;
+    st = ensure_pinned(ctx, kPinnedBytes);
     if (st != GCMC_OK) return st;
     float r2lo, r2hi;
     bool wrap;
@@ -916,11 +934,19 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
     k_sum_partials<<<1, 1024, 0, ctx->stream>>>(part, ctx->ncell, width, res);
     ctx->launches += 2;
     GCMC_CUDA(ctx, cudaGetLastError());
-    double h[2 + 2 * kMaxSpecies * kMaxSpecies];
+    double *hp = (double *)ctx->h_pinned + 16;
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp, res, width * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GCMC_CUDA(ctx, cudaMemcpyAsync(hp + width, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return GCMC_OK;
+}
+
+gcmc_status energy_grad_finish(gcmc_ctx *ctx, double *deps, double *dsigma, double *energy, double *virial)
+{
+    const int S = ctx->S;
+    const int width = 2 + 2 * S * S;
+    const double *h = (const double *)ctx->h_pinned + 16;
     int bits = 0;
-    GCMC_CUDA(ctx, cudaMemcpyAsync(h, res, width * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    GCMC_CUDA(ctx, cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    memcpy(&bits, h + width, sizeof(int));
     if (bits & kStatusTimeout)
         return fail(ctx, GCMC_ERR_TIMEOUT, "gcmc_energy_grad: a bulk copy did not complete within the wait limit");
     if (energy) *energy = h[0];
@@ -930,6 +956,55 @@ gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma
             if (deps) deps[a * S + b] = h[2 + a * S + b];
             if (dsigma) dsigma[a * S + b] = h[2 + S * S + a * S + b] / ctx->sigma[a * kMaxSpecies + b];
         }
+    return GCMC_OK;
+}
+
+gcmc_status energy_grad(gcmc_ctx *ctx, float *dpos, double *deps, double *dsigma, double *energy,
+                        double *virial)
+{
+    gcmc_status st = energy_grad_begin(ctx, dpos);
+    if (st != GCMC_OK) return st;
+    GCMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return energy_grad_finish(ctx, deps, dsigma, energy, virial);
+}
+
+// ---- the configuration as real coordinates -----------------------------
+__global__ void k_export(const uint4 *__restrict__ pos_by_id, const int64_t *__restrict__ d_n, int S, int64_t maxN,
+                         double h, double *__restrict__ pos, int32_t *__restrict__ species)
+{
+    __shared__ long long base[kMaxSpecies + 1];
+    if (threadIdx.x == 0) {
+        long long b = 0;
+        for (int s = 0; s < S; ++s) {
+            base[s] = b;
+            b += d_n[s];
+        }
+        base[S] = b;
+    }
+    __syncthreads();
+    const long long N = base[S];
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (r >= base[s + 1]) ++s;
+        const uint4 v = pos_by_id[(long long)s * maxN + (r - base[s])];
+        // the centre of the grid cell quantises back to the same grid point
+        pos[3 * r + 0] = ((double)v.x + 0.5) * h;
+        pos[3 * r + 1] = ((double)v.y + 0.5) * h;
+        pos[3 * r + 2] = ((double)v.z + 0.5) * h;
+        species[r] = s;
+    }
+}
+
+gcmc_status export_positions(gcmc_ctx *ctx, double *pos, int32_t *species)
+{
+    int64_t N = 0;
+    for (int s = 0; s < ctx->S; ++s) N += ctx->n_host[s];
+    if (N == 0) return GCMC_OK;
+    k_export<<<blocks_for(ctx, N, 256), 256, 0, ctx->stream>>>(ctx->pos_by_id, ctx->d_n, ctx->S, ctx->maxN, ctx->h,
+                                                              pos, species);
+    ctx->launches += 1;
+    GCMC_CUDA(ctx, cudaGetLastError());
     return GCMC_OK;
 }
 

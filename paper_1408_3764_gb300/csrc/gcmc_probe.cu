@@ -79,6 +79,52 @@ static cudaError_t time_launch(cudaStream_t st, float *ms, void (*launch)(cudaSt
     return e;
 }
 
+// Throughput of the arithmetic pipes: every thread runs 8 independent
+// dependent chains (FMA, or the reciprocal of the special-function unit),
+// enough warps per SM to cover their latency.  The result goes to sink only
+// so that the work is kept.
+template <typename R>
+__global__ void __launch_bounds__(256) k_probe_fma(int64_t n, R *sink)
+{
+    R a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (R)(threadIdx.x + k) * (R)1e-3;
+    const R b = (R)0.999999, c = (R)1e-7;
+    for (int64_t i = 0; i < n; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == (R)-1) *sink = s;
+}
+
+__global__ void __launch_bounds__(256) k_probe_rcp(int64_t n, float *sink)
+{
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0f + (float)(threadIdx.x + k) * 1e-3f;
+    for (int64_t i = 0; i < n; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float r;
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[k]));
+            a[k] = r + 1.0f;  // each reciprocal depends on the last (1 / (1 + x) stays in [0.5, 1])
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1.f) *sink = s;
+}
+
+struct PipeArg {
+    int64_t n;
+    int blocks;
+    void *sink;
+};
+
 struct ChaseArg {
     const uint32_t *next;
     int64_t hops;
@@ -151,5 +197,41 @@ extern "C" gcmc_status gcmc_probe_latency(void *stream, int64_t bytes, gcmc_prob
     if (d_next) cudaFree(d_next);
     if (d_sink) cudaFree(d_sink);
     if (d_dsink) cudaFree(d_dsink);
+    return e == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
+}
+
+extern "C" gcmc_status gcmc_probe_pipes(void *stream, gcmc_pipe_peaks *out)
+{
+    if (!out) return GCMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    void *d_sink = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_sink, 16);
+    const int blocks = sms * 8;  // 64 warps per SM
+    const double threads = (double)blocks * 256.0;
+    float ms = 0.f;
+    PipeArg a32{4096, blocks, d_sink}, a64{256, blocks, d_sink}, ar{1024, blocks, d_sink};
+    if (e == cudaSuccess)
+        e = time_launch(st, &ms, [](cudaStream_t s, void *p) {
+            PipeArg *c = (PipeArg *)p;
+            k_probe_fma<float><<<c->blocks, 256, 0, s>>>(c->n, (float *)c->sink);
+        }, &a32);
+    out->fp32_tflops = threads * 8.0 * 2.0 * (double)a32.n / (ms * 1e-3) / 1e12;
+    if (e == cudaSuccess)
+        e = time_launch(st, &ms, [](cudaStream_t s, void *p) {
+            PipeArg *c = (PipeArg *)p;
+            k_probe_fma<double><<<c->blocks, 256, 0, s>>>(c->n, (double *)c->sink);
+        }, &a64);
+    out->fp64_tflops = threads * 8.0 * 2.0 * (double)a64.n / (ms * 1e-3) / 1e12;
+    if (e == cudaSuccess)
+        e = time_launch(st, &ms, [](cudaStream_t s, void *p) {
+            PipeArg *c = (PipeArg *)p;
+            k_probe_rcp<<<c->blocks, 256, 0, s>>>(c->n, (float *)c->sink);
+        }, &ar);
+    out->mufu_gops = threads * 8.0 * (double)ar.n / (ms * 1e-3) / 1e9;
+    out->sms = sms;
+    if (d_sink) cudaFree(d_sink);
     return e == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
 }

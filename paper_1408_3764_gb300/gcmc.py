@@ -130,6 +130,22 @@ class Box:
         self._n_build = pos.shape[0]
         return self
 
+    def export_positions(self, pos_buf: Optional[torch.Tensor] = None, species_buf: Optional[torch.Tensor] = None):
+        """The current configuration as build_cells input (device [N, 3] FP64 and [N] int32,
+        species-major): building from it reproduces the configuration.  Given buffers
+        (large enough) are filled without a host synchronisation; the N rows in use are returned."""
+        n = int(self.counts().sum())
+        if pos_buf is None:
+            pos_buf = torch.empty((max(n, 1), 3), dtype=torch.float64, device=self.device)
+        if species_buf is None:
+            species_buf = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        if pos_buf.shape[0] < n or species_buf.shape[0] < n:
+            raise ValueError("export buffers hold %d rows, %d needed" % (min(pos_buf.shape[0], species_buf.shape[0]), n))
+        out = C.c_int64()
+        check(self._lib.gcmc_export_positions(self._h, _ptr(pos_buf), _ptr(species_buf), C.byref(out)), self._h,
+              "gcmc_export_positions")
+        return pos_buf[: out.value], species_buf[: out.value]
+
     def cell_list(self):
         """The last build's compact cell list: (cell starts, cell counts, input indices sorted by cell)."""
         g = self.geometry()
@@ -361,6 +377,33 @@ class Batch:
             return stats, [b[:n_moves].cpu().numpy().copy().view(TRACE_DTYPE).reshape(-1) for b in bufs]
         return stats
 
+    def prepare(self, positions: Sequence[torch.Tensor], species: Sequence[torch.Tensor]) -> np.ndarray:
+        """Builds every box's cells from device tensors ([n_k, 3] FP64, [n_k] int32) and
+        returns the full-system energies (two host synchronisations in all)."""
+        K = len(self.boxes)
+        pp = (C.c_void_p * K)(*[p.data_ptr() for p in positions])
+        sp = (C.c_void_p * K)(*[t.data_ptr() for t in species])
+        n = np.ascontiguousarray([int(p.shape[0]) for p in positions], dtype=np.int64)
+        e = np.zeros(K, np.float64)
+        rc = self._lib.gcmc_batch_prepare(self._h, pp, sp, n.ctypes.data_as(C.c_void_p), e.ctypes.data_as(C.c_void_p))
+        if rc != 0:
+            raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
+        return e
+
+    def energy_grad(self, dpos: Optional[Sequence[Optional[torch.Tensor]]] = None):
+        """Forces (into the given device tensors, [N_k, 3] FP32, species-major), energies and
+        virials of every box (one host synchronisation in all)."""
+        K = len(self.boxes)
+        dp = None
+        if dpos is not None:
+            dp = (C.c_void_p * K)(*[(t.data_ptr() if t is not None else None) for t in dpos])
+        e = np.zeros(K, np.float64)
+        w = np.zeros(K, np.float64)
+        rc = self._lib.gcmc_batch_energy_grad(self._h, dp, e.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p))
+        if rc != 0:
+            raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
+        return e, w
+
     def config(self, set_config: int = -2):
         """Sets the team shape (-1 automatic, -2 unchanged); returns it and the tuner's per-shape times."""
         out = C.c_int32()
@@ -390,35 +433,76 @@ def species_major_order(species) -> np.ndarray:
     return np.argsort(s, kind="stable")
 
 
+class _BoxCache:
+    """A few contexts kept for the differentiable energy, keyed by box, cutoff,
+    force-field tables, precision and device, so that repeated calls build
+    cells in an existing context instead of creating and freeing one."""
+
+    def __init__(self, size: int = 4):
+        self.size = size
+        self.items = []  # (key, Box), most recent last
+        self.builds = 0  # cell builds done through the cache (counts reuse in tests)
+        self.creates = 0
+
+    def get(self, L, rc, eps, sigma, precision, device) -> "Box":
+        key = (float(L), float(rc), tuple(np.asarray(eps, np.float64).ravel().tolist()),
+               tuple(np.asarray(sigma, np.float64).ravel().tolist()), precision, str(device))
+        for i, (k, b) in enumerate(self.items):
+            if k == key:
+                self.items.append(self.items.pop(i))
+                return b
+        b = Box(L, rc, eps, sigma, precision=precision, device=device)
+        self.creates += 1
+        self.items.append((key, b))
+        if len(self.items) > self.size:
+            self.items.pop(0)[1].close()
+        return b
+
+
+_box_cache = _BoxCache()
+
+
 class _CellListEnergy(torch.autograd.Function):
-    """Full-system cell-list energy with its hand-written backward (the
-    gradient kernel evaluates dE/dpos, dE/deps and dE/dsigma in one pass)."""
+    """Full-system cell-list energy with its hand-written backward.  The
+    forward pass bins the positions into a cached context and runs the
+    energy kernel only; the backward pass runs the gradient kernel (dE/dpos,
+    dE/deps, dE/dsigma in one pass) on the same cells, rebinning first if
+    another call used the context in between."""
 
     @staticmethod
     def forward(ctx, pos, eps, sigma, species, L, rc, precision):
-        box = Box(L, rc, eps.detach().cpu().numpy(), sigma.detach().cpu().numpy(), precision=precision,
-                  device=pos.device if pos.is_cuda else None)
-        box.build_cells(pos.detach().to(torch.float64), species)
-        g = box.energy_grad(want_pos=pos.requires_grad)
-        box.close()
-        sm = torch.as_tensor(species_major_order(species.detach().cpu().numpy()), device=pos.device)
-        dpos = None
-        if g["dpos"] is not None:
-            dpos = torch.empty_like(g["dpos"])
-            dpos[sm] = g["dpos"]
-            dpos = dpos.to(pos.dtype)
-        ctx.save_for_backward(dpos if dpos is not None else torch.empty(0),
-                              torch.as_tensor(g["deps"], dtype=eps.dtype),
-                              torch.as_tensor(g["dsigma"], dtype=sigma.dtype))
-        ctx.has_pos = dpos is not None
-        return torch.tensor(g["energy"], dtype=torch.float64, device=pos.device)
+        device = pos.device if pos.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        box = _box_cache.get(L, rc, eps.detach().cpu().numpy(), sigma.detach().cpu().numpy(), precision, device)
+        pos64 = pos.detach().to(device=device, dtype=torch.float64).contiguous()
+        box.build_cells(pos64, species)
+        _box_cache.builds += 1
+        box._token = ctx.token = object()  # the cells in the context now belong to this call
+        E = box.total_energy()
+        ctx.box = box
+        ctx.pos64 = pos64
+        ctx.species = species
+        ctx.pos_dtype = pos.dtype
+        ctx.e_dtype, ctx.s_dtype = eps.dtype, sigma.dtype
+        return torch.tensor(E, dtype=torch.float64, device=pos.device)
 
     @staticmethod
     def backward(ctx, go):
-        dpos, deps, dsig = ctx.saved_tensors
-        gp = (go.to(dpos.dtype) * dpos) if ctx.has_pos else None
-        ge = go.cpu().to(deps.dtype) * deps
-        gs = go.cpu().to(dsig.dtype) * dsig
+        box = ctx.box
+        if getattr(box, "_token", None) is not ctx.token:
+            box.build_cells(ctx.pos64, ctx.species)
+            _box_cache.builds += 1
+            box._token = ctx.token
+        g = box.energy_grad(want_pos=ctx.needs_input_grad[0])
+        gp = None
+        if ctx.needs_input_grad[0]:
+            sm = torch.as_tensor(species_major_order(ctx.species.detach().cpu().numpy()), device=g["dpos"].device)
+            dpos = torch.empty_like(g["dpos"])
+            dpos[sm] = g["dpos"]  # species-major rows back to input order
+            gp = go.to(dpos.dtype) * dpos
+            gp = gp.to(ctx.pos_dtype)
+        ge = go.detach().cpu().to(ctx.e_dtype) * torch.as_tensor(g["deps"], dtype=ctx.e_dtype)
+        gs = go.detach().cpu().to(ctx.s_dtype) * torch.as_tensor(g["dsigma"], dtype=ctx.s_dtype)
+        ctx.box = None
         return gp, ge, gs, None, None, None, None
 
 

@@ -387,6 +387,7 @@ def test_chain_energy_bookkeeping():
 
 
 def test_gradient_autograd_function():
+    from paper_1408_3764_gb300 import gcmc as G
     from paper_1408_3764_gb300.gcmc import cell_list_energy
     L, n = 10.0, 400
     pos = torch.tensor(_relaxed(n, L, 31), dtype=torch.float32, device="cuda", requires_grad=True)
@@ -407,3 +408,23 @@ def test_gradient_autograd_function():
     assert np.allclose(pos.grad.cpu().numpy(), want, atol=1e-4 * fs, rtol=1e-4)
     assert np.allclose(e_t.grad.numpy(), ref["deps"], rtol=1e-4)
     assert np.allclose(s_t.grad.numpy(), ref["dsigma"], rtol=1e-4)
+    # repeated calls reuse one context; a forward-only call runs no gradient
+    creates = G._box_cache.creates
+    for _ in range(3):
+        pos.grad = None
+        E2 = cell_list_energy(pos, e_t.detach(), s_t.detach(), types, L, 2.5, "fp32")
+        E2.backward()
+        assert E2.item() == E.item()
+        assert np.allclose(pos.grad.cpu().numpy(), want, atol=1e-4 * fs, rtol=1e-4)
+    assert G._box_cache.creates == creates
+    with torch.no_grad():
+        E3 = cell_list_energy(pos, e_t, s_t, types, L, 2.5, "fp32")
+    assert E3.item() == E.item()
+    # two forwards, then the first one's backward: its cells are rebuilt
+    p2 = (pos.detach() * 0.999).requires_grad_(True)
+    Ea = cell_list_energy(pos, e_t.detach(), s_t.detach(), types, L, 2.5, "fp32")
+    Eb = cell_list_energy(p2, e_t.detach(), s_t.detach(), types, L, 2.5, "fp32")
+    pos.grad = None
+    Ea.backward()
+    assert np.allclose(pos.grad.cpu().numpy(), want, atol=1e-4 * fs, rtol=1e-4)
+    del Eb

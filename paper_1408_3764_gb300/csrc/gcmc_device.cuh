@@ -159,6 +159,24 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// g (< 2^63) as a float-float hi + lo, with 32-bit conversions and integer
+// operations only (64-bit integer conversions run on the FP64 pipe, a small
+// fraction of the FP32 one): hi approximates g, the integer value of hi is
+// rebuilt from its bits, and the exact remainder g - hi (|r| < 2^40) is
+// converted as (r >> 16) * 2^16 + (r & 0xFFFF), both parts exact in FP32.
+__device__ __forceinline__ void split_u64(unsigned long long g, float &hi, float &lo)
+{
+    const uint32_t gh = (uint32_t)(g >> 32), gl = (uint32_t)g;
+    hi = fmaf(__uint2float_rn(gh), 4294967296.0f, __uint2float_rn(gl));
+    // the integer value of hi: mantissa shifted by its exponent
+    const uint32_t bits = __float_as_uint(hi);
+    const int ex = (int)(bits >> 23) - 150;  // hi = mant * 2^ex
+    const unsigned long long mant = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+    const unsigned long long hv = ex >= 0 ? (mant << ex) : (mant >> -ex);
+    const long long r = (long long)(g - hv);
+    lo = fmaf(__int2float_rn((int)(r >> 16)), 65536.0f, __uint2float_rn((uint32_t)r & 0xFFFFu));
+}
+
 __device__ __forceinline__ void lj_ff(int ex, int ey, int ez, float ch, float cl, float sh, float sl, float &uh,
                                       float &ul, float &m)
 {
@@ -171,8 +189,8 @@ __device__ __forceinline__ void lj_ff(int ex, int ey, int ez, float ch, float cl
         m = uh;
         return;
     }
-    const float r2h = __ull2float_rn(g);
-    const float r2l = __ll2float_rn((long long)(g - __float2ull_rz(r2h)));
+    float r2h, r2l;
+    split_u64(g, r2h, r2l);
     const float rcp = rcp_approx(r2h);
     // s^2 = q + ql: the residual (sh + sl) - q (r2h + r2l) divided by r^2
     const float q = __fmul_rn(sh, rcp);

@@ -103,10 +103,10 @@ __device__ __forceinline__ uint32_t quantize_dev(double x, double q, bool &ok)
 // wrapped once more into [-L/2, L/2] (wrap = 1).  The queued pairs use the
 // exact wrapped integer difference p - q.
 // ---------------------------------------------------------------------------
-constexpr int kBuf = 1024;    // staged records per pass
+constexpr int kBuf = 896;     // staged records per pass (six CTAs fit an SM)
 constexpr int kPChunk = 64;   // points per chunk (per-point sums in shared memory)
 constexpr int kNbWarps = 8;   // warps of a neighbourhood CTA
-constexpr int kNbQ = 64;      // queue entries per warp (a ring)
+constexpr int kNbQ = 128;     // queue entries per warp (a ring: up to 31 + 2 x 32 pending)
 
 // Grid coordinate of the centre of cell k along an axis of T cells.
 __device__ __forceinline__ uint32_t cell_centre(int k, int T)
@@ -130,21 +130,28 @@ struct __align__(16) NbShared {
 struct NbQueue {
     int *buf;
     int head, n;
+    unsigned lt;  // this lane's mask of lower lanes
 };
 
+// Adds the lanes' entries of two screened candidates (where in0 / in1) to
+// the queue; evaluates 32 at a time while 32 or more are pending.
 template <typename Drain>
-__device__ __forceinline__ void nb_push(NbQueue &Q, bool in, int f, Drain &D)
+__device__ __forceinline__ void nb_push2(NbQueue &Q, bool in0, int f0, bool in1, int f1, Drain &D)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned bm = __ballot_sync(0xffffffffu, in);
-    if (bm == 0u) return;
-    if (in) Q.buf[(Q.head + Q.n + __popc(bm & ((1u << lane) - 1u))) & (kNbQ - 1)] = f;
-    Q.n += __popc(bm);
+    const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
+    if ((b0 | b1) == 0u) return;
+    const int base = Q.head + Q.n, n0 = __popc(b0);
+    if (in0) Q.buf[(base + __popc(b0 & Q.lt)) & (kNbQ - 1)] = f0;
+    if (in1) Q.buf[(base + n0 + __popc(b1 & Q.lt)) & (kNbQ - 1)] = f1;
+    Q.n += n0 + __popc(b1);
     if (Q.n >= 32) {
         __syncwarp();
-        D(Q.buf[(Q.head + lane) & (kNbQ - 1)], true);
-        Q.head = (Q.head + 32) & (kNbQ - 1);
-        Q.n -= 32;
+        do {
+            D(Q.buf[(Q.head + lane) & (kNbQ - 1)], true);
+            Q.head = (Q.head + 32) & (kNbQ - 1);
+            Q.n -= 32;
+        } while (Q.n >= 32);
         __syncwarp();
     }
 }
@@ -174,33 +181,40 @@ __device__ __forceinline__ float wrap_grid(float d)
 
 template <typename Skip, typename Drain>
 __device__ __forceinline__ void nb_screen(const NbShared &sh, int nst, const uint4 &P, const float3 &pf, uint64_t R2,
-                                          float r2lo, float r2hi, bool wrap, NbQueue &Q, Skip skip, Drain &D)
+                                          float r2lo, float r2hi, bool wrap, NbQueue &Q, Skip skip, Drain &D,
+                                          int tag = 0)
 {
     const int lane = threadIdx.x & 31;
-    for (int b = 0; b < nst; b += 32) {
-        const int f = b + lane;
-        bool in = false, band = false;
-        if (f < nst) {
-            const float4 q = sh.fl[f];
-            if (!skip(f, __float_as_uint(q.w))) {
-                float dx = pf.x - q.x, dy = pf.y - q.y, dz = pf.z - q.z;
-                if (wrap) {
-                    dx = wrap_grid(dx);
-                    dy = wrap_grid(dy);
-                    dz = wrap_grid(dz);
+    // two candidates per lane and pass (f and f + 32)
+    for (int b = 0; b < nst; b += 64) {
+        bool in[2], band[2];
+        int f[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            f[u] = b + 32 * u + lane;
+            in[u] = band[u] = false;
+            if (f[u] < nst) {
+                const float4 q = sh.fl[f[u]];
+                if (!skip(f[u], __float_as_uint(q.w))) {
+                    float dx = pf.x - q.x, dy = pf.y - q.y, dz = pf.z - q.z;
+                    if (wrap) {
+                        dx = wrap_grid(dx);
+                        dy = wrap_grid(dy);
+                        dz = wrap_grid(dz);
+                    }
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    in[u] = r2 < r2lo;
+                    band[u] = r2 >= r2lo && r2 <= r2hi;
                 }
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                in = r2 < r2lo;
-                band = r2 >= r2lo && r2 <= r2hi;
             }
         }
-        if (__any_sync(0xffffffffu, band)) {
-            if (band) {
-                const GridSep s = grid_sep(P, sh.raw[f]);
-                in = s.g < R2;
-            }
+        // inside the thin band around rc^2 the exact integer test decides
+        if (__any_sync(0xffffffffu, band[0] || band[1])) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (band[u]) in[u] = grid_sep(P, sh.raw[f[u]]).g < R2;
         }
-        nb_push(Q, in, f, D);
+        nb_push2(Q, in[0], f[0] | tag, in[1], f[1] | tag, D);
     }
 }
 
@@ -290,12 +304,15 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_trial_energy(
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
+    // per-point sums over the passes: FP32 mode float-float (hi, lo) and
+    // uabs in .z; FP64 mode energy and uabs in .x, .y
     __shared__ double2 part[kPChunk];
+    __shared__ float4 partf[kPChunk];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
     __syncthreads();
     unsigned parity = 0;
-    NbQueue Q = {sh.q[w], 0, 0};
+    NbQueue Q = {sh.q[w], 0, 0, (1u << lane) - 1u};
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int p0 = ps[c], p1 = ps[c + 1];
         if (p1 == p0) continue;  // uniform across the block
@@ -308,7 +325,10 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_trial_energy(
         for (int pb = p0; pb < p1; pb += kPChunk) {
             const int pn = min(kPChunk, p1 - pb);
             __syncthreads();  // the previous chunk's sums have been written out
-            for (int i = threadIdx.x; i < pn; i += blockDim.x) part[i] = make_double2(0.0, 0.0);
+            for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+                if constexpr (F32) partf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                else part[i] = make_double2(0.0, 0.0);
+            }
             for (int base = 0; base < max(total, 1); base += kBuf) {
                 const int nst = min(kBuf, total - base);
                 if (!nb_stage(sh, cpos, base, base + max(nst, 0), cx0, cy0, cz0, parity, status)) return;
@@ -320,26 +340,35 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_trial_energy(
                     nb_screen(sh, max(nst, 0), tp.P, pf, R2, r2lo, r2hi, wrap, Q,
                               [&](int, uint32_t tag) { return tag == ex; }, D);
                     nb_flush(Q, D);
-                    double e, a;
                     if constexpr (F32) {
                         const FF s = ff_warp_sum(FF{D.eh, D.el});
-                        e = (double)s.hi + (double)s.lo;
-                        a = (double)warp_sum(D.mag);
+                        const float a = warp_sum(D.mag);
+                        if (lane == 0) {
+                            const FF t = ff_add(FF{partf[i].x, partf[i].y}, s);
+                            partf[i] = make_float4(t.hi, t.lo, partf[i].z + a, 0.f);
+                        }
                     } else {
-                        e = warp_sum(D.de);
-                        a = warp_sum(D.da);
-                    }
-                    if (lane == 0) {
-                        part[i].x += e;
-                        part[i].y += a;
+                        const double e = warp_sum(D.de), a = warp_sum(D.da);
+                        if (lane == 0) {
+                            part[i].x += e;
+                            part[i].y += a;
+                        }
                     }
                 }
             }
             __syncthreads();
             for (int i = threadIdx.x; i < pn; i += blockDim.x) {
                 const int k = pts[pb + i].idx;
-                out[k] = part[i].x;
-                if (out_abs) out_abs[k] = part[i].y;
+                double e, a;
+                if constexpr (F32) {
+                    e = (double)partf[i].x + (double)partf[i].y;
+                    a = (double)partf[i].z;
+                } else {
+                    e = part[i].x;
+                    a = part[i].y;
+                }
+                out[k] = e;
+                if (out_abs) out_abs[k] = a;
             }
         }
     }
@@ -394,20 +423,27 @@ __global__ void k_trial_place(const TrialPt *__restrict__ tmp, const int32_t *__
 }
 
 // ---- full-system energy ---------------------------------------------------
+// Queue entries of the full-system energy: the staged partner's index in
+// the low 16 bits, the home particle's index in the chunk above them, so
+// that the pairs of several home particles share one evaluation pass.
 template <bool F32>
 struct PairDrain {
     const NbShared &sh;
-    uint4 P;
-    int t;
+    const uint4 *home;
     const FieldF &ff;
     const FieldD &fd;
     float eh = 0.f, el = 0.f, wh = 0.f, wl = 0.f;
     double de = 0.0, dw = 0.0;
-    __device__ PairDrain(const NbShared &s, const FieldF &f, const FieldD &d) : sh(s), ff(f), fd(d) {}
-    __device__ __forceinline__ void operator()(int f, bool have)
+    __device__ PairDrain(const NbShared &s, const uint4 *h, const FieldF &f, const FieldD &d)
+        : sh(s), home(h), ff(f), fd(d)
+    {
+    }
+    __device__ __forceinline__ void operator()(int e, bool have)
     {
         if (!have) return;
-        const uint4 r = sh.raw[f];
+        const uint4 P = home[e >> 16];
+        const int t = (int)tag_species(P.w);
+        const uint4 r = sh.raw[e & 0xFFFF];
         const int k = t * kMaxSpecies + (int)tag_species(r.w);
         const int ex = (int)(P.x - r.x), ey = (int)(P.y - r.y), ez = (int)(P.z - r.z);
         if constexpr (F32) {
@@ -445,15 +481,16 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_energy(const uint4 *__re
     extern __shared__ __align__(128) unsigned char dyn[];
     NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
     __shared__ double red[kNbWarps][2];
+    __shared__ float2 redf[kNbWarps][2];
     __shared__ uint4 home[kPChunk];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
     __syncthreads();
     unsigned parity = 0;
-    NbQueue Q = {sh.q[w], 0, 0};
+    NbQueue Q = {sh.q[w], 0, 0, (1u << lane) - 1u};
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int h0 = cs[c], nh = cs[c + 1] - h0;
-        PairDrain<F32> D(sh, ff, fd);
+        PairDrain<F32> D(sh, home, ff, fd);
         if (nh > 0) {
             const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
             __syncthreads();
@@ -470,40 +507,45 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_energy(const uint4 *__re
                     if (!nb_stage(sh, cpos, base, base + nst, cx0, cy0, cz0, parity, status)) return;
                     for (int i = w; i < pn; i += kNbWarps) {
                         const int hi = pb + i;  // the particle's item index (home items come first)
-                        D.P = home[i];
-                        D.t = (int)tag_species(D.P.w);
-                        const float3 pf =
-                            make_float3(rel_f(D.P.x, cx0), rel_f(D.P.y, cy0), rel_f(D.P.z, cz0));
-                        nb_screen(sh, nst, D.P, pf, R2, r2lo, r2hi, wrap, Q,
+                        const uint4 P = home[i];
+                        const float3 pf = make_float3(rel_f(P.x, cx0), rel_f(P.y, cy0), rel_f(P.z, cz0));
+                        nb_screen(sh, nst, P, pf, R2, r2lo, r2hi, wrap, Q,
                                   [&](int f, uint32_t) {
                                       const int g = base + f;
                                       return g < nh && g <= hi;
                                   },
-                                  D);
-                        nb_flush(Q, D);
+                                  D, i << 16);
                     }
+                    nb_flush(Q, D);  // before the staged records are replaced
                 }
             }
         }
-        double e, vw;
         if constexpr (F32) {
+            // float-float across the warp and the block, one FP64 value per sum
             const FF s = ff_warp_sum(FF{D.eh, D.el});
             const FF v = ff_warp_sum(FF{D.wh, D.wl});
-            e = (double)s.hi + (double)s.lo;
-            vw = (double)v.hi + (double)v.lo;
+            if (lane == 0) {
+                redf[w][0] = make_float2(s.hi, s.lo);
+                redf[w][1] = make_float2(v.hi, v.lo);
+            }
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                FF sum = {0.f, 0.f};
+                for (int k = 0; k < kNbWarps; ++k) sum = ff_add(sum, FF{redf[k][threadIdx.x].x, redf[k][threadIdx.x].y});
+                partial[2 * c + threadIdx.x] = (double)sum.hi + (double)sum.lo;
+            }
         } else {
-            e = warp_sum(D.de);
-            vw = warp_sum(D.dw);
-        }
-        if (lane == 0) {
-            red[w][0] = e;
-            red[w][1] = vw;
-        }
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            double sum = 0.0;
-            for (int k = 0; k < kNbWarps; ++k) sum += red[k][threadIdx.x];
-            partial[2 * c + threadIdx.x] = sum;
+            const double e = warp_sum(D.de), vw = warp_sum(D.dw);
+            if (lane == 0) {
+                red[w][0] = e;
+                red[w][1] = vw;
+            }
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                double sum = 0.0;
+                for (int k = 0; k < kNbWarps; ++k) sum += red[k][threadIdx.x];
+                partial[2 * c + threadIdx.x] = sum;
+            }
         }
         __syncthreads();
     }
@@ -573,7 +615,7 @@ struct GradDrain {
                                      (unsigned long long)((long long)ez * ez);
         R r2, c4e, sig2;
         if constexpr (F32) {
-            r2 = __ull2float_rn(g);
+            r2 = fmaf(__uint2float_rn((uint32_t)(g >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)g));
             c4e = ff.c4e[k];
             sig2 = ff.sig2[k];
         } else {
@@ -621,8 +663,13 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__rest
     extern __shared__ __align__(128) unsigned char dyn[];
     NbShared &sh = *reinterpret_cast<NbShared *>(dyn);
     __shared__ double red[kNbWarps][kW];
-    __shared__ double fpart[kPChunk][3];
+    __shared__ double fpart[kPChunk][3];   // FP64 mode: per-point forces over the passes
+    __shared__ float2 fpartf[kPChunk][3];  // FP32 mode: the same as float-float
     __shared__ uint4 home[kPChunk];
+    // FP32 mode with up to two species: each warp's scalar sums of a cell in
+    // float-float registers (the same in every lane), written once per cell
+    constexpr bool kRegSums = F32 && NS <= 2;
+    FF sE = {0.f, 0.f}, sW = {0.f, 0.f}, sEp[NS][NS], sSg[NS][NS];
     __shared__ long long base_s[kMaxSpecies];  // first species-major row of each species
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int width = 2 + 2 * S * S;
@@ -637,9 +684,16 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__rest
     for (int k = threadIdx.x; k < kNbWarps * kW; k += blockDim.x) (&red[0][0])[k] = 0.0;
     __syncthreads();
     unsigned parity = 0;
-    NbQueue Q = {sh.q[w], 0, 0};
+    NbQueue Q = {sh.q[w], 0, 0, (1u << lane) - 1u};
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int h0 = cs[c], nh = cs[c + 1] - h0;
+        if constexpr (kRegSums) {
+            sE = sW = FF{0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) sEp[a][q] = sSg[a][q] = FF{0.f, 0.f};
+        }
         if (nh > 0) {
             const int cx = (int)(c % T), cy = (int)((c / T) % T), cz = (int)(c / ((int64_t)T * T));
             __syncthreads();
@@ -652,7 +706,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__rest
                 __syncthreads();
                 for (int i = threadIdx.x; i < pn; i += blockDim.x) {
                     home[i] = cpos[h0 + pb + i];
-                    fpart[i][0] = fpart[i][1] = fpart[i][2] = 0.0;
+                    if constexpr (F32) fpartf[i][0] = fpartf[i][1] = fpartf[i][2] = make_float2(0.f, 0.f);
+                    else fpart[i][0] = fpart[i][1] = fpart[i][2] = 0.0;
                 }
                 for (int base = 0; base < total; base += kBuf) {
                     const int nst = min(kBuf, total - base);
@@ -667,35 +722,78 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__rest
                         nb_screen(sh, nst, D.P, pf, R2, r2lo, r2hi, wrap, Q,
                                   [&](int, uint32_t tag) { return tag == self; }, D);
                         nb_flush(Q, D);
-                        const double gx = warp_sum((double)D.fx), gy = warp_sum((double)D.fy),
-                                     gz = warp_sum((double)D.fz);
-                        double vE, vW;
+                        // FP32 mode reduces across the warp and accumulates in
+                        // float-float (the FP64 pipe is a small fraction of the
+                        // FP32 one); FP64 mode in FP64
                         if constexpr (F32) {
-                            const FF s = ff_warp_sum(FF{D.eh, D.el});
-                            const FF v = ff_warp_sum(FF{D.wh, D.wl});
-                            vE = (double)s.hi + (double)s.lo;
-                            vW = (double)v.hi + (double)v.lo;
-                        } else {
-                            vE = warp_sum(D.de);
-                            vW = warp_sum(D.dw);
-                        }
-                        double ve[NS], vs[NS];
+                            const FF gx = ff_warp_sum(FF{D.fx, 0.f}), gy = ff_warp_sum(FF{D.fy, 0.f}),
+                                     gz = ff_warp_sum(FF{D.fz, 0.f});
+                            const FF vE = ff_warp_sum(FF{D.eh, D.el}), vW = ff_warp_sum(FF{D.wh, D.wl});
+                            if (lane == 0) {
+                                const FF ox = ff_add(FF{fpartf[i][0].x, fpartf[i][0].y}, gx);
+                                const FF oy = ff_add(FF{fpartf[i][1].x, fpartf[i][1].y}, gy);
+                                const FF oz = ff_add(FF{fpartf[i][2].x, fpartf[i][2].y}, gz);
+                                fpartf[i][0] = make_float2(ox.hi, ox.lo);
+                                fpartf[i][1] = make_float2(oy.hi, oy.lo);
+                                fpartf[i][2] = make_float2(oz.hi, oz.lo);
+                            }
+                            if constexpr (kRegSums) {
+                                sE = ff_add(sE, vE);
+                                sW = ff_add(sW, vW);
 #pragma unroll
-                        for (int q = 0; q < NS; ++q) {
-                            ve[q] = warp_sum((double)D.aEps[q]);
-                            vs[q] = warp_sum((double)D.aSig[q]);
-                        }
-                        if (lane == 0) {
-                            fpart[i][0] += gx;
-                            fpart[i][1] += gy;
-                            fpart[i][2] += gz;
-                            red[w][0] += vE;
-                            red[w][1] += vW;
+                                for (int q = 0; q < NS; ++q) {
+                                    const FF ve = ff_warp_sum(FF{D.aEps[q], 0.f});
+                                    const FF vs = ff_warp_sum(FF{D.aSig[q], 0.f});
+#pragma unroll
+                                    for (int tt = 0; tt < NS; ++tt) {
+                                        if (tt == D.t) {
+                                            sEp[tt][q] = ff_add(sEp[tt][q], ve);
+                                            sSg[tt][q] = ff_add(sSg[tt][q], vs);
+                                        }
+                                    }
+                                }
+                            } else {
+                                double ve[NS], vs[NS];
+#pragma unroll
+                                for (int q = 0; q < NS; ++q) {
+                                    FF x = ff_warp_sum(FF{D.aEps[q], 0.f}), y = ff_warp_sum(FF{D.aSig[q], 0.f});
+                                    ve[q] = (double)x.hi + (double)x.lo;
+                                    vs[q] = (double)y.hi + (double)y.lo;
+                                }
+                                if (lane == 0) {
+                                    red[w][0] += (double)vE.hi + (double)vE.lo;
+                                    red[w][1] += (double)vW.hi + (double)vW.lo;
+#pragma unroll
+                                    for (int q = 0; q < NS; ++q) {
+                                        if (q < S) {
+                                            red[w][2 + D.t * S + q] += ve[q];
+                                            red[w][2 + S * S + D.t * S + q] += vs[q];
+                                        }
+                                    }
+                                }
+                            }
+                        } else {
+                            const double gx = warp_sum((double)D.fx), gy = warp_sum((double)D.fy),
+                                         gz = warp_sum((double)D.fz);
+                            const double vE = warp_sum(D.de), vW = warp_sum(D.dw);
+                            double ve[NS], vs[NS];
 #pragma unroll
                             for (int q = 0; q < NS; ++q) {
-                                if (q < S) {
-                                    red[w][2 + D.t * S + q] += ve[q];
-                                    red[w][2 + S * S + D.t * S + q] += vs[q];
+                                ve[q] = q < S ? warp_sum((double)D.aEps[q]) : 0.0;
+                                vs[q] = q < S ? warp_sum((double)D.aSig[q]) : 0.0;
+                            }
+                            if (lane == 0) {
+                                fpart[i][0] += gx;
+                                fpart[i][1] += gy;
+                                fpart[i][2] += gz;
+                                red[w][0] += vE;
+                                red[w][1] += vW;
+#pragma unroll
+                                for (int q = 0; q < NS; ++q) {
+                                    if (q < S) {
+                                        red[w][2 + D.t * S + q] += ve[q];
+                                        red[w][2 + S * S + D.t * S + q] += vs[q];
+                                    }
                                 }
                             }
                         }
@@ -706,11 +804,33 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_grad(const uint4 *__rest
                     for (int i = threadIdx.x; i < pn; i += blockDim.x) {
                         const uint32_t tg = home[i].w;
                         const int64_t row = base_s[tag_species(tg)] + tag_index(tg);
-                        dpos[3 * row + 0] = (float)(fpart[i][0] * inv_h);
-                        dpos[3 * row + 1] = (float)(fpart[i][1] * inv_h);
-                        dpos[3 * row + 2] = (float)(fpart[i][2] * inv_h);
+                        if constexpr (F32) {
+                            const float ih = (float)inv_h;
+                            dpos[3 * row + 0] = (fpartf[i][0].x + fpartf[i][0].y) * ih;
+                            dpos[3 * row + 1] = (fpartf[i][1].x + fpartf[i][1].y) * ih;
+                            dpos[3 * row + 2] = (fpartf[i][2].x + fpartf[i][2].y) * ih;
+                        } else {
+                            dpos[3 * row + 0] = (float)(fpart[i][0] * inv_h);
+                            dpos[3 * row + 1] = (float)(fpart[i][1] * inv_h);
+                            dpos[3 * row + 2] = (float)(fpart[i][2] * inv_h);
+                        }
                     }
                 }
+            }
+        }
+        if constexpr (kRegSums) {
+            if (lane == 0) {
+                red[w][0] = (double)sE.hi + (double)sE.lo;
+                red[w][1] = (double)sW.hi + (double)sW.lo;
+#pragma unroll
+                for (int a2 = 0; a2 < NS; ++a2)
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        if (a2 < S && q < S) {
+                            red[w][2 + a2 * S + q] = (double)sEp[a2][q].hi + (double)sEp[a2][q].lo;
+                            red[w][2 + S * S + a2 * S + q] = (double)sSg[a2][q].hi + (double)sSg[a2][q].lo;
+                        }
+                    }
             }
         }
         __syncthreads();

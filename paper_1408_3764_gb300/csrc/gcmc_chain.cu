@@ -90,6 +90,7 @@ struct ChainArgs {
     double beta, lnV;
     double logz[kMaxSpecies];
     double tol;  // relative tolerance that defines "near the threshold"
+    float beta_f, tol_f;  // beta and tol in FP32 (the FP32 Metropolis test)
     unsigned long long wait_ns;  // limit of every wait (kWaitNs unless a test shortens it)
     int stall_at;  // diagnostic: the committer waits on a flag nothing sets at this move (-1 none)
     int virial;  // also keep the running virial sum_{i<j} r U'(r)
@@ -292,7 +293,7 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
 __device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, float ln_ns, float ln_ns1, float lnu,
                                           float dUf, float uab)
 {
-    const float beta_f = (float)a.beta, tol_f = (float)a.tol;
+    const float beta_f = a.beta_f, tol_f = a.tol_f;
     float lnK = 0.f;
     if (type == 1) lnK = a.lnzv_f[sp] - ln_ns1;
     else if (type == 2) lnK = ln_ns - a.lnzv_f[sp];
@@ -305,7 +306,10 @@ __device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, 
 
 // ---------------------------------------------------------------- the chain
 // VIR: the evaluations also sum the virial change dW of each trial.
-constexpr int kQ = 64;  // entries of an evaluator warp's queue of pair terms inside the cutoff
+// entries of an evaluator warp's queue of pair terms inside the cutoff: at
+// most 31 wait between drains, and one item adds at most 64
+constexpr int kQ = 128;
+constexpr int kMaxEW = 14;  // evaluator warps, at most (queues in dynamic shared memory)
 constexpr int kChainWarps = 16;  // warps of a chain CTA (committer, keeper, evaluators, idle)
 
 template <bool F32, bool VIR>
@@ -529,51 +533,50 @@ struct Chain {
         }
     }
 
-    // Adds the lanes' entries (where `in`) to the queue; drains 32 when full.
-    __device__ __forceinline__ void push(FQ &Q, bool in, const int4 &ent, const ItemK &K, Acc32 &A) const
+    // Adds the lanes' entries (where `in`) to the queue.
+    __device__ __forceinline__ void enqueue(FQ &Q, bool in, const int4 &ent) const
     {
         const unsigned bm = __ballot_sync(0xffffffffu, in);
         if (bm == 0u) return;
         if (in) Q.buf[(Q.head + Q.n + __popc(bm & ((1u << lane) - 1u))) & (kQ - 1)] = ent;
         Q.n += __popc(bm);
-        if (Q.n >= 32) {
+    }
+
+    // Evaluates queued terms, 32 at a time (fewer for the last), while at
+    // least `thr` wait.  One loop serves the whole evaluation, so the long
+    // compensated pair term appears once in the kernel's code.
+    __device__ __forceinline__ void drain_while(FQ &Q, int thr, const ItemK &K, Acc32 &A) const
+    {
+#pragma unroll 1
+        while (Q.n >= thr) {
+            const int c = min(Q.n, 32);
             __syncwarp();
-            drain(Q, 32, K, A);
-            Q.head = (Q.head + 32) & (kQ - 1);
-            Q.n -= 32;
+            drain(Q, c, K, A);
+            Q.head = (Q.head + c) & (kQ - 1);
+            Q.n -= c;
             __syncwarp();
         }
     }
 
-    template <int SIDES>
+    // TWO: both positions of a displacement; else the old position of a
+    // deletion or the new one of an insertion.  Each separation is converted
+    // from its exact integer value (the new one is not the old separation
+    // plus the displacement in FP32, which would round the longer old one).
+    template <bool TWO>
     __device__ __forceinline__ void item32(const Trial &t, const uint4 &q, bool valid, uint32_t fl,
-                                           const ItemK &K, FQ &Q, Acc32 &A) const
+                                           const ItemK &K, FQ &Q) const
     {
         const bool use = valid && (q.w != t.Po.w);
         const int kk = K.single ? 0 : (int)t.s * kMaxSpecies + (int)tag_species(q.w);
-        // SIDES 1: the old position only (deletion); 2: the new only
-        // (insertion); 3: both (displacement)
-        const uint4 &P0 = (SIDES == 2) ? t.Pn : t.Po;
-        const int dx = (int)(P0.x - q.x), dy = (int)(P0.y - q.y), dz = (int)(P0.z - q.z);
-        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        const bool del = t.type == 2;
 #pragma unroll
-        for (int side = 0; side < (SIDES == 3 ? 2 : 1); ++side) {
-            int ex = dx, ey = dy, ez = dz;
-            float gx = fx, gy = fy, gz = fz;
-            if (SIDES == 3 && side == 1) {
-                // the new separation is converted from its exact integer
-                // value: old separation + displacement in FP32 would round
-                // the (possibly long) old separation first
-                ex = (int)(t.Pn.x - q.x);
-                ey = (int)(t.Pn.y - q.y);
-                ez = (int)(t.Pn.z - q.z);
-                gx = (float)ex;
-                gy = (float)ey;
-                gz = (float)ez;
-            }
-            const uint32_t need = (SIDES == 3) ? (side ? kNew : kOld) : (SIDES == 2 ? kNew : kOld);
+        for (int side = 0; side < (TWO ? 2 : 1); ++side) {
+            const bool old = TWO ? side == 0 : del;
+            const uint32_t px = old ? t.Po.x : t.Pn.x, py = old ? t.Po.y : t.Pn.y, pz = old ? t.Po.z : t.Pn.z;
+            const int ex = (int)(px - q.x), ey = (int)(py - q.y), ez = (int)(pz - q.z);
+            const float gx = (float)ex, gy = (float)ey, gz = (float)ez;
             const float r2f = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            const bool want = use && (fl & need);
+            const bool want = use && (fl & (old ? kOld : kNew));
             bool in = want && (r2f < K.r2lo);
             // inside the thin band around rc^2 the exact integer test decides
             const bool band = want && r2f >= K.r2lo && r2f <= K.r2hi;
@@ -585,8 +588,7 @@ struct Chain {
                     in = g < a.R2;
                 }
             }
-            const bool neg = (SIDES == 1) || (SIDES == 3 && side == 0);
-            push(Q, in, make_int4(ex, ey, ez, kk | (neg ? 0x100 : 0)), K, A);
+            enqueue(Q, in, make_int4(ex, ey, ez, kk | (old ? 0x100 : 0)));
         }
     }
 
@@ -608,12 +610,11 @@ struct Chain {
 
     template <bool P32>
     __device__ __forceinline__ void item(const Trial &t, const uint4 &q, bool valid, uint32_t fl, const ItemK &K,
-                                         FQ &Q, Acc32 &A, double &de, double &da, double &dw) const
+                                         FQ &Q, double &de, double &da, double &dw) const
     {
         if constexpr (P32) {
-            if (t.type == 0) item32<3>(t, q, valid, fl, K, Q, A);
-            else if (t.type == 1) item32<2>(t, q, valid, fl, K, Q, A);
-            else item32<1>(t, q, valid, fl, K, Q, A);
+            if (t.type == 0) item32<true>(t, q, valid, fl, K, Q);
+            else item32<false>(t, q, valid, fl, K, Q);
         } else if (valid && q.w != t.Po.w) {
             FF e0 = {0.f, 0.f};
             float u0 = 0.f;
@@ -701,21 +702,41 @@ struct Chain {
                                       : make_uint4(0, 0, 0, 0xFFFFFFFEu);
 #pragma unroll
             for (int u = 0; u < KU; ++u) {
-                const bool v = cell[u] >= 0;
-                if (v && (flg[u] & kOld) && cell[u] == t.co) {
+                if (cell[u] >= 0 && (flg[u] & kOld) && cell[u] == t.co) {
                     if (q[u].w == t.Po.w) o.self_slot = slot[u];
                     else if (slot[u] == ncl[u] - 1) {
                         o.has_last = 1;
                         o.last = q[u];
                     }
                 }
-                item<P32>(t, q[u], v, flg[u], K, Q, A, de, da, dw);
+            }
+            if constexpr (P32) {
+                // one item at a time (not unrolled), then the queue's full
+                // batches: the screen and the pair term appear once in code
+#pragma unroll 1
+                for (int u = 0; u < KU; ++u) {
+                    uint4 qu = q[0];
+                    uint32_t fu = flg[0];
+                    int cu = cell[0];
+#pragma unroll
+                    for (int i = 1; i < KU; ++i)
+                        if (u == i) {
+                            qu = q[i];
+                            fu = flg[i];
+                            cu = cell[i];
+                        }
+                    item<true>(t, qu, cu >= 0, fu, K, Q, de, da, dw);
+                    drain_while(Q, 32, K, A);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < KU; ++u) item<false>(t, q[u], cell[u] >= 0, flg[u], K, Q, de, da, dw);
             }
         }
         o.w = 0.f;
         o.dw = 0.0;
         if constexpr (P32) {
-            if (Q.n > 0) drain(Q, Q.n, K, A);
+            drain_while(Q, 1, K, A);
             __syncwarp();
             const FF e = ff_warp_sum(FF{A.eh, A.el});
             o.e = e.hi;
@@ -917,7 +938,11 @@ __device__ __forceinline__ bool box_within(const uint4 &X0, const uint4 &X1, con
 // Whether the committed moves [j0, j1) left a trial's evaluation standing:
 // none of them touched its old cell or wrote its particle's record, and
 // none put, removed or moved a particle within rc of its old or new
-// position.  Warp-wide (one lane per logged move); the result is uniform.
+// position.  Warp-wide, four lanes per logged move (eight moves a pass):
+// lane 4i + k tests, for move j0 + i, the positions it wrote (k = 0, 1) or
+// the entry it moved (k = 2, 3) against the trial's old (k even) or new
+// (k odd) position; lane 4i also compares cells and records.  The result is
+// uniform.
 template <bool F32, bool VIR>
 __device__ __forceinline__ bool logs_ok(const Chain<F32, VIR> &C, const Shared &sh, const Trial &t, int j0, int j1,
                                         int lane)
@@ -925,21 +950,24 @@ __device__ __forceinline__ bool logs_ok(const Chain<F32, VIR> &C, const Shared &
     bool bad = false;
     const ChainArgs &a = C.a;
     if (t.possible) {
-        const bool old_side = t.type != 1, new_side = t.type != 2;
+        const int k = lane & 3;
+        const bool side = (k & 1) ? t.type != 2 : t.type != 1;
+        const bool old_side = t.type != 1;
         const int myid = ((int)t.s << 24) | t.idx;
+        const uint4 P = (k & 1) ? t.Pn : t.Po;
         const unsigned long long R2 = a.R2;
         const uint32_t rcg = (uint32_t)a.rcg;
-        for (int j = j0 + lane; j < j1; j += 32) {
-            // the five words of the log entry, loaded together
+        for (int j = j0 + (lane >> 2); j < j1; j += 8) {
+            // the log entry's words, loaded together
             const LogRec &L = sh.logs[j & (kRS - 1)];
             const int4 h = L.head, id = L.ids;
-            const uint4 X0 = L.pos0, X1r = L.pos1, Mv = L.moved;
+            const uint4 X0 = (k < 2) ? L.pos0 : L.moved;
+            const uint4 X1r = (k < 2) ? L.pos1 : L.moved;
             if (!(h.x & 1)) continue;
-            const uint4 X1 = ((id.w & 0xFF) == 2) ? X1r : X0;
             // the old cell's slots (self, last entry) must be as seen, and
             // the particle's record must be as read
-            if (old_side && (h.y == t.co || h.z == t.co || h.w == t.co || id.x == myid || id.y == myid ||
-                             id.z == myid))
+            if (k == 0 && old_side &&
+                (h.y == t.co || h.z == t.co || h.w == t.co || id.x == myid || id.y == myid || id.z == myid))
                 bad = true;
             // a particle that appeared, vanished or moved within rc of the
             // trial's old or new position changes dU (exact integer cutoff,
@@ -947,12 +975,9 @@ __device__ __forceinline__ bool logs_ok(const Chain<F32, VIR> &C, const Shared &
             // moved into the freed slot (an evaluation that read the older
             // count may have met it twice).  Changes farther away add
             // nothing: their pair terms are exactly zero.
-            if (old_side && box_within(X0, X1, t.Po, R2, rcg)) bad = true;
-            if (new_side && box_within(X0, X1, t.Pn, R2, rcg)) bad = true;
-            if (id.w >> 8) {
-                if (old_side && box_within(Mv, Mv, t.Po, R2, rcg)) bad = true;
-                if (new_side && box_within(Mv, Mv, t.Pn, R2, rcg)) bad = true;
-            }
+            const bool use = side && (k < 2 || (id.w >> 8) != 0);
+            const uint4 X1 = (k < 2 && (id.w & 0xFF) == 2) ? X1r : X0;
+            if (use && box_within(X0, X1, P, R2, rcg)) bad = true;
         }
     }
     return !__any_sync(0xffffffffu, bad);
@@ -1016,9 +1041,12 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
     constexpr int EW = G * NTEAM;
     constexpr int NW = kChainWarps;
     constexpr int NTH = NW * 32;
-    static_assert(EW + 2 <= NW, "team shape");
+    static_assert(EW + 2 <= NW && EW <= kMaxEW, "team shape");
+    // dynamic shared memory: the evaluator warps' pair-term queues (FP32
+    // runs), then the cell counters
     extern __shared__ __align__(16) unsigned char dyn[];
-    uint16_t *cnt = (uint16_t *)dyn;
+    int4 *fq = (int4 *)dyn;
+    uint16_t *cnt = (uint16_t *)(dyn + (F32 ? kMaxEW * kQ * sizeof(int4) : 0));
     unsigned long long t_start = 0;
     if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     __shared__ Shared sh;
@@ -1043,8 +1071,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         }
         return;
     }
-    // the evaluator warps' queues of pair terms (FP32 runs)
-    __shared__ int4 fq[F32 ? EW * kQ : 1];
     Chain<F32, VIR> C(a, sh, cnt, fq);
     const int tid = threadIdx.x, lane = C.lane, warp = C.warp, T = C.T;
     const int n = a.n_moves;
@@ -1190,7 +1216,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                             sk = Sk.t.s;
                             const float dU = F32 ? Sk.th : (float)Sk.td;
                             const float lnK = (ty == 1) ? a.lnzv_f[sk] - sh.ln_n1[sk] : sh.ln_n[sk] - a.lnzv_f[sk];
-                            if (Wk.lnu < lnK - (float)a.beta * dU) d = (ty == 1) ? 1 : -1;
+                            if (Wk.lnu < lnK - a.beta_f * dU) d = (ty == 1) ? 1 : -1;
                         } else if (ty != 0 && vload(sh.likely[ty - 1])) {
                             sk = (int)__umulhi(Wk.w[5], (uint32_t)a.S);
                             d = (ty == 1) ? 1 : -1;
@@ -1402,7 +1428,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 e.hi = S.th;
                 e.lo = S.tl;
                 uab = S.tu;
-                dW = (double)S.tw;
+                dW = VIR ? (double)S.tw : 0.0;
             } else {
                 de = S.td;
                 da = S.ta;
@@ -1422,7 +1448,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 // decide in FP64: in FP32 mode the whole trial is evaluated
                 // again in FP64 (pair terms and sums)
                 if constexpr (F32) {
-                    const typename Chain<F32, VIR>::Part Q = C.template eval_part<false, 4>(t, 0, 1);
+                    const typename Chain<F32, VIR>::Part Q = C.template eval_part<false, 1>(t, 0, 1);
                     de = Q.de;
                     da = Q.da;
                     dW = Q.dw;
@@ -1722,6 +1748,8 @@ static void fill_args(ChainArgs &a, const ChainJob &j, ChainOut *out)
     a.lnV = std::log(ctx->V);
     for (int s = 0; s < kMaxSpecies; ++s) a.logz[s] = s < ctx->S ? mix->log_z[s] : 0.0;
     a.tol = ctx->precision == GCMC_FP32 ? 1e-5 : 1e-12;
+    a.beta_f = (float)a.beta;
+    a.tol_f = (float)a.tol;
     a.virial = (mix->flags & GCMC_MIX_VIRIAL) ? 1 : 0;
     a.wait_ns = ctx->wait_ns ? ctx->wait_ns : kWaitNs;
     a.stall_at = (ctx->stall_at >= j.done && ctx->stall_at - j.done < a.n_moves) ? (int)(ctx->stall_at - j.done) : -1;
@@ -1812,6 +1840,7 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
     }
     size_t smem = 16;
     for (auto &j : jobs) smem = std::max(smem, ((size_t)j.ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16);
+    if (f32) smem += kMaxEW * kQ * sizeof(int4);
     // the virial sums are compiled in only when a chain of the launch keeps it
     bool vir = false;
     for (auto &j : jobs) vir |= (j.mix.flags & GCMC_MIX_VIRIAL) != 0;
@@ -2010,9 +2039,9 @@ static gcmc_status run_jobs_tuned(std::vector<ChainJob> &jobs, cudaStream_t st, 
 static gcmc_status check_chain_fits(gcmc_ctx *ctx)
 {
     const size_t smem = ((size_t)ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16;
-    // static shared memory: the chain state, its arguments, the evaluator
-    // warps' pair-term queues (at most 14 warps) and a margin for the rest
-    const size_t queues = 14 * kQ * sizeof(int4);
+    // the chain state and its arguments (static), the evaluator warps'
+    // pair-term queues (dynamic, FP32 runs) and a margin for the rest
+    const size_t queues = ctx->precision == GCMC_FP32 ? kMaxEW * kQ * sizeof(int4) : 0;
     if (smem + sizeof(Shared) + sizeof(ChainArgs) + queues + 4096 > ctx->smem_optin)
         return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: too many cells for the on-chip cell counters");
     if (ctx->T > 1023) return fail(ctx, GCMC_ERR_INVALID_ARG, "gcmc_run_moves: more than 1023 cells per side");

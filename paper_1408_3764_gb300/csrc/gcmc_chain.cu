@@ -197,6 +197,7 @@ struct Slot {  // evaluators -> committer, one per move in flight
     int c0;                       // moves committed when the evaluation started
     int arrive;                   // warps finished
     int tag;                      // move + 1 of the evaluation under way, 0 none
+    int tpub;                     // move + 1 whose trial (t, nsu) is published, 0 none
     int pseq[kGMax];              // per warp: count epoch its work-cell counts were read in (-1 torn)
     int nsu[kMaxSpecies];         // the particle counts the evaluation picked its particle with
     int acc0;                     // accepted moves (at most) when the evaluation started
@@ -1096,6 +1097,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
     }
     for (int k = tid; k < kRS; k += NTH) {
         sh.slots[k].tag = 0;
+        sh.slots[k].tpub = 0;
         sh.slots[k].arrive = 0;
         sh.book[k].ready = 0;
         sh.logs[k].head.x = 0;
@@ -1183,6 +1185,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                     S.self_slot = -1;
                     S.has_last = 0;
                     S.arrive = 0;
+                    S.tpub = 0;
                     S.c0 = c0;
                     S.acc0 = acc0;
                     __threadfence_block();
@@ -1246,15 +1249,24 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             const int m = tc.m[p];
             const Trial t = C.make_trial(m, tc.ns[p]);
             Slot &S = sh.slots[(m) & (kRS - 1)];
+            // the trial and the counts it picked with, published before the
+            // evaluation: the committer checks them while the team evaluates
+            if (j == 0) {
+                if (lane < a.S) S.nsu[lane] = tc.ns[p][lane];
+                if (lane == 0) S.t = t;
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    vstore(S.tpub, m + 1);
+                }
+            }
             const typename Chain<F32, VIR>::Part P = C.template eval_part<F32, KU>(t, j, G);
             if (P.self_slot >= 0) S.self_slot = P.self_slot;
             if (P.has_last) {
                 S.last_val = P.last;
                 S.has_last = 1;
             }
-            if (j == 0 && lane < a.S) S.nsu[lane] = tc.ns[p][lane];
             if (lane == 0) {
-                if (j == 0) S.t = t;
                 S.pseq[j] = P.seq;
                 if constexpr (F32) {
                     S.ph[j] = P.e;
@@ -1358,7 +1370,8 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             int c0 = 0, attempt = 0;
             Trial tcur;
             for (;; ++attempt) {
-                // wait for the evaluation of m and for room in the keeper's book
+                // wait for the trial of m (its evaluation under way) and for
+                // room in the keeper's book
                 const unsigned long long tw = clock64();
                 Wait wt;
                 for (;;) {
@@ -1366,7 +1379,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                     if (lane == 0) {
                         const int tg = vload(S.tag);
                         __threadfence_block();
-                        r = tg == m + 1 && vload(S.arrive) == G + 1 && m < vload(sh.booked) + kRS;
+                        r = tg == m + 1 && vload(S.tpub) == m + 1 && m < vload(sh.booked) + kRS;
                     }
                     r = __shfl_sync(0xffffffffu, r, 0);
                     if (r) break;
@@ -1385,27 +1398,49 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 __threadfence_block();
                 c0 = S.c0;
                 tcur = S.t;  // one copy in registers for the checks and the decision
-                // the team's warps must have read the counts of one epoch
-                // (their item ranges follow the counts)
-                // no move accepted since the evaluation started: nothing it
-                // read has changed (counts, records, cells), only the pick
-                // is left to check
+                // While the team evaluates, check what does not depend on its
+                // sums (the moves [c0, m) are all committed by now).  The
+                // counts at the move's turn equal those the evaluation picked
+                // with: the same particle (else compare the picks).  No move
+                // accepted since the evaluation started: nothing it read has
+                // changed (counts, records, cells).
                 const bool quiet = S.acc0 == nacc;
-                const int q0 = S.pseq[0];
-                const bool one_epoch = quiet || (__all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0);
-                const unsigned long long tv1 = clock64();
-                bool valid = c0 == m || quiet || (one_epoch && logs_ok(C, sh, tcur, c0, m, lane));
-                const unsigned long long tv2 = clock64();
-                // the counts at the move's turn equal those the evaluation
-                // picked with: the same particle (else compare the picks)
                 const bool same_counts =
                     __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == sh.ns_ring[m & (kRS - 1)][lane]);
-                valid = valid && (c0 == m || same_counts || pick_ok(C, sh, tcur, m));
+                const bool pick = c0 == m || same_counts || pick_ok(C, sh, tcur, m);
+                const unsigned long long tv1 = clock64();
+                const bool logs = !pick || c0 == m || quiet || logs_ok(C, sh, tcur, c0, m, lane);
+                const unsigned long long tv2 = clock64();
+                // then wait for the team's sums
+                Wait wa;
+                for (;;) {
+                    int r = 0;
+                    if (lane == 0) r = vload(S.arrive) == G + 1;
+                    r = __shfl_sync(0xffffffffu, r, 0);
+                    if (r) break;
+                    if (wa.expired(a.wait_ns)) {
+                        if (lane == 0) {
+                            atomicOr(&sh.status, kStatusTimeout);
+                            atomicOr(&sh.where, 2);
+                        }
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) break;
                 const unsigned long long tv3 = clock64();
-                cv += tv3 - tv;
-                cv_e += tv1 - tv;
+                cw += tv3 - tv2;
+                __threadfence_block();
+                // the team's warps must have read the counts of one epoch
+                // (their item ranges follow the counts)
+                const int q0 = S.pseq[0];
+                const bool one_epoch = quiet || (__all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0);
+                const bool valid = pick && (c0 == m || quiet || (one_epoch && logs));
+                const unsigned long long tv4 = clock64();
+                cv += (tv2 - tv) + (tv4 - tv3);
+                cv_p += tv1 - tv;
                 cv_l += tv2 - tv1;
-                cv_p += tv3 - tv2;
+                cv_e += tv4 - tv3;
                 if (valid) break;
                 // evaluate again against the configuration after m moves
                 if (lane == 0) {

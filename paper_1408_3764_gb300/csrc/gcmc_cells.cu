@@ -308,8 +308,6 @@ gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species
     uint4 *grid = (uint4 *)(base + o_grid);
     int32_t *cellid = (int32_t *)(base + o_cell);
     int32_t *sidx = (int32_t *)(base + o_sidx);
-    int32_t *tmp = (int32_t *)(base + o_tmp);
-    int32_t *fill = (int32_t *)(base + o_fill);
     int32_t *bc = (int32_t *)(base + o_bc);
     int32_t *part = (int32_t *)(base + o_part);
     int64_t *small = (int64_t *)(base + o_small);  // [0..7] species totals, [8] max count (int)

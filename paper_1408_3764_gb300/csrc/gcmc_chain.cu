@@ -1720,8 +1720,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
 // evaluate more moves ahead (better when moves rarely conflict); larger
 // teams evaluate one move faster (better when N changes often).
 constexpr int kNumConfigs = 4;
-static const int kConfigG[kNumConfigs] = {7, 4, 3, 2};
-static const int kConfigT[kNumConfigs] = {2, 3, 4, 6};
 
 template <bool F32, bool VIR>
 static void *chain_kernel(int config)

@@ -418,9 +418,8 @@ class Runner:
             if N[i] > self.pos[i].shape[0]:  # rare: a chain grew past its buffers
                 self._alloc(2 * N[i] + 1024, i)
         eg, wg = self.batch.energy_grad([self.dpos[i][: N[i]] for i in range(K)])
-        for i in range(K):
-            self.boxes[i].export_positions(self.pos[i], self.typ[i])
-            self.n[i] = N[i]
+        self.batch.export_positions(self.pos, self.typ)
+        self.n = list(N)
         if self.host_inputs:
             for i in range(K):
                 with torch.cuda.stream(self.box_streams[i]):

@@ -406,6 +406,14 @@ gcmc_status gcmc_batch_prepare(gcmc_batch *batch, const double *const *pos, cons
  * Errors: as gcmc_energy_grad, the first failing chain's. */
 gcmc_status gcmc_batch_energy_grad(gcmc_batch *batch, float *const *dpos, double *energies, double *virials);
 
+/* gcmc_export_positions for every chain of the batch (no paper counterpart:
+ * the next step's build input).  pos, species: host arrays of n_chains
+ * device pointers, each large enough for that chain's N; n: host, n_chains
+ * counts out, or NULL.  Launches one kernel per chain on its context's
+ * stream; nothing waits.  Errors: as gcmc_export_positions, the first
+ * failing chain's; INVALID_ARG (NULL arrays). */
+gcmc_status gcmc_batch_export_positions(gcmc_batch *batch, double *const *pos, int32_t *const *species, int64_t *n);
+
 /* Per-chain move records for the following gcmc_batch_run_moves calls:
  * traces is a host array of n_chains device pointers, each NULL or room for
  * the n_moves records (gcmc_trace, the format of gcmc_run_moves) of a call,

@@ -97,6 +97,7 @@ SIGNATURES = {
     "gcmc_batch_set_traces": (C.c_int, [_vp, _vp]),
     "gcmc_batch_prepare": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gcmc_batch_energy_grad": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gcmc_batch_export_positions": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gcmc_batch_config": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "gcmc_batch_launches": (C.c_int, [_vp, _vp]),
     "gcmc_batch_device_ms": (C.c_int, [_vp, C.POINTER(C.c_double)]),

@@ -4,6 +4,7 @@
 // gcmc_energy.cu, gcmc_chain.cu and gcmc_micro.cu.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -703,6 +704,17 @@ static gcmc_status batch_fail(gcmc_batch *b, int k, gcmc_status st)
     return st;
 }
 
+// Calls f(k) for every box k in order; the first failing box's status,
+// with its message in the batch, or OK.
+static gcmc_status batch_each(gcmc_batch *b, const std::function<gcmc_status(int)> &f)
+{
+    for (int k = 0; k < (int)b->ctxs.size(); ++k) {
+        const gcmc_status st = f(k);
+        if (st != GCMC_OK) return batch_fail(b, k, st);
+    }
+    return GCMC_OK;
+}
+
 static gcmc_status batch_sync(gcmc_batch *b)
 {
     for (size_t k = 0; k < b->ctxs.size(); ++k) {
@@ -727,14 +739,14 @@ gcmc_status gcmc_batch_prepare(gcmc_batch *b, const double *const *pos, const in
             return GCMC_ERR_INVALID_ARG;
         }
     }
-    gcmc_status st;
-    for (int k = 0; k < K; ++k)
-        if ((st = build_begin(b->ctxs[k], pos[k], species[k], n[k])) != GCMC_OK) return batch_fail(b, k, st);
+    gcmc_status st = batch_each(b, [&](int k) { return build_begin(b->ctxs[k], pos[k], species[k], n[k]); });
+    if (st != GCMC_OK) return st;
     if ((st = batch_sync(b)) != GCMC_OK) return st;
-    for (int k = 0; k < K; ++k) {
-        if ((st = build_finish(b->ctxs[k])) != GCMC_OK) return batch_fail(b, k, st);
-        if ((st = total_energy_begin(b->ctxs[k])) != GCMC_OK) return batch_fail(b, k, st);
-    }
+    st = batch_each(b, [&](int k) {
+        const gcmc_status s1 = build_finish(b->ctxs[k]);
+        return s1 != GCMC_OK ? s1 : total_energy_begin(b->ctxs[k]);
+    });
+    if (st != GCMC_OK) return st;
     if ((st = batch_sync(b)) != GCMC_OK) return st;
     for (int k = 0; k < K; ++k)
         if ((st = total_energy_finish(b->ctxs[k], energies ? energies + k : nullptr)) != GCMC_OK)
@@ -746,17 +758,26 @@ gcmc_status gcmc_batch_energy_grad(gcmc_batch *b, float *const *dpos, double *en
 {
     if (!b) return GCMC_ERR_INVALID_ARG;
     const int K = (int)b->ctxs.size();
-    gcmc_status st;
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k)
         if (!b->ctxs[k]->built) return batch_fail(b, k, fail(b->ctxs[k], GCMC_ERR_STATE, "cells not built"));
-        if ((st = energy_grad_begin(b->ctxs[k], dpos ? dpos[k] : nullptr)) != GCMC_OK) return batch_fail(b, k, st);
-    }
+    gcmc_status st = batch_each(b, [&](int k) { return energy_grad_begin(b->ctxs[k], dpos ? dpos[k] : nullptr); });
+    if (st != GCMC_OK) return st;
     if ((st = batch_sync(b)) != GCMC_OK) return st;
     for (int k = 0; k < K; ++k)
         if ((st = energy_grad_finish(b->ctxs[k], nullptr, nullptr, energies ? energies + k : nullptr,
                                      virials ? virials + k : nullptr)) != GCMC_OK)
             return batch_fail(b, k, st);
     return GCMC_OK;
+}
+
+gcmc_status gcmc_batch_export_positions(gcmc_batch *b, double *const *pos, int32_t *const *species, int64_t *n)
+{
+    if (!b) return GCMC_ERR_INVALID_ARG;
+    if (!pos || !species) {
+        b->err = "gcmc_batch_export_positions: NULL arrays";
+        return GCMC_ERR_INVALID_ARG;
+    }
+    return batch_each(b, [&](int k) { return gcmc_export_positions(b->ctxs[k], pos[k], species[k], n ? n + k : nullptr); });
 }
 
 gcmc_status gcmc_batch_set_traces(gcmc_batch *b, gcmc_trace *const *traces)

@@ -404,6 +404,23 @@ class Batch:
             raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
         return e, w
 
+    def export_positions(self, positions: Sequence[torch.Tensor], species: Sequence[torch.Tensor]) -> np.ndarray:
+        """Every box's current configuration into the given device tensors ([>= N_k, 3] FP64,
+        [>= N_k] int32, species-major; build input for the next prepare) without a host
+        synchronisation; returns the counts N_k."""
+        K = len(self.boxes)
+        for k in range(K):
+            need = int(self.boxes[k].counts().sum())
+            if positions[k].shape[0] < need or species[k].shape[0] < need:
+                raise ValueError("export buffers of box %d hold fewer than %d rows" % (k, need))
+        pp = (C.c_void_p * K)(*[p.data_ptr() for p in positions])
+        sp = (C.c_void_p * K)(*[t.data_ptr() for t in species])
+        n = np.zeros(K, np.int64)
+        rc = self._lib.gcmc_batch_export_positions(self._h, pp, sp, n.ctypes.data_as(C.c_void_p))
+        if rc != 0:
+            raise _lib.GcmcError(rc, self._lib.gcmc_batch_last_error(self._h).decode(errors="replace"))
+        return n
+
     def config(self, set_config: int = -2):
         """Sets the team shape (-1 automatic, -2 unchanged); returns it and the tuner's per-shape times."""
         out = C.c_int32()

@@ -169,6 +169,17 @@ def test_batched_prepare_and_gradient_match_per_box_calls(precision):
         g = b.energy_grad()
         assert eg[k] == g["energy"] and wg[k] == g["virial"]
         assert torch.equal(dpos[k], g["dpos"])
+    # the batched export writes what the per-box export writes (buffers may
+    # be longer than N; a shorter one is refused before anything is written)
+    n = [int(b.counts().sum()) for b in boxes]
+    bp = [torch.empty((n[k] + 5, 3), dtype=torch.float64, device="cuda") for k in range(len(boxes))]
+    bt = [torch.empty(n[k] + 5, dtype=torch.int32, device="cuda") for k in range(len(boxes))]
+    assert list(batch.export_positions(bp, bt)) == n
+    for k, b in enumerate(boxes):
+        p, s = b.export_positions()
+        assert torch.equal(bp[k][: n[k]], p) and torch.equal(bt[k][: n[k]], s)
+    with pytest.raises(ValueError):
+        batch.export_positions([x[:1] for x in bp], bt)
     # export and rebuild: the same configuration, particle for particle (the
     # order within a cell follows the ids after a build, the move history
     # before it)

@@ -1405,9 +1405,16 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 // accepted since the evaluation started: nothing it read has
                 // changed (counts, records, cells).
                 const bool quiet = S.acc0 == nacc;
-                const bool same_counts =
-                    __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == sh.ns_ring[m & (kRS - 1)][lane]);
-                const bool pick = c0 == m || same_counts || pick_ok(C, sh, tcur, m);
+                const int *ring = sh.ns_ring[m & (kRS - 1)];
+                bool pick = c0 == m || tcur.type == 1;
+                if (!pick && (tcur.type == 2 || a.S == 1)) {
+                    // one count decides the pick: idx = floor(w1 n / 2^32)
+                    const int na = ring[tcur.type == 2 ? (int)tcur.s : 0];
+                    pick = tcur.possible ? (na > 0 && (int)__umulhi(C.words(m).w[1], (uint32_t)na) == tcur.idx)
+                                         : na == 0;
+                } else if (!pick) {
+                    pick = __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == ring[lane]) || pick_ok(C, sh, tcur, m);
+                }
                 const unsigned long long tv1 = clock64();
                 const bool logs = !pick || c0 == m || quiet || logs_ok(C, sh, tcur, c0, m, lane);
                 const unsigned long long tv2 = clock64();

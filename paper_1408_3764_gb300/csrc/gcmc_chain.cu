@@ -1029,12 +1029,12 @@ struct TeamCtl {
     int ns[2][kMaxSpecies];
 };
 
-// NTEAM teams of G evaluator warps (warps 1 .. G * NTEAM), the committer
-// (warp 0) and the keeper (last warp).  Team k evaluates moves k, k + NTEAM,
-// k + 2 NTEAM, ..., each as soon as fewer than LOOK moves separate it from
-// the committer; a move the committer finds invalid goes back to its team,
-// ahead of the team's new moves.  KU: slots per work cell a lane loads at
-// once.
+// NTEAM teams of G evaluator warps, the committer (warp 0) and the keeper
+// (warp 4).  Team k evaluates moves k, k + NTEAM, k + 2 NTEAM, ..., each as
+// soon as fewer than LOOK moves separate it from the committer; a move the
+// committer finds invalid is evaluated again by the first team free to take
+// it, ahead of that team's new moves.  KU: slots per work cell a lane loads
+// at once.
 template <bool F32, bool VIR, int G, int NTEAM, int LOOK, int KU>
 __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
@@ -1052,7 +1052,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
     if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     __shared__ Shared sh;
     __shared__ TeamCtl ctl[NTEAM];
-    __shared__ int redo[NTEAM];  // move + 1 to evaluate again, 0 none
+    __shared__ int redo;  // move + 1 to evaluate again (the first free team takes it), 0 none
     __shared__ unsigned long long team_cyc[3];  // leaders' idle cycles, evaluation cycles, evaluations
     // this CTA's chain: its arguments copied to shared memory
     __shared__ __align__(16) ChainArgs a;
@@ -1102,7 +1102,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         sh.book[k].ready = 0;
         sh.logs[k].head.x = 0;
     }
-    if (tid < NTEAM) redo[tid] = 0;
+    if (tid == 0) redo = 0;
     if (tid < 3) team_cyc[tid] = 0ull;
     if (tid == 0) {
         sh.committed = 0;
@@ -1145,7 +1145,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                     const int acc_seen = vload(sh.nacc);
                     __threadfence_block();
                     const int com = vload(sh.committed);
-                    const int rd = vload(redo[team]);
+                    const int rd = vload(redo);
                     const bool fresh = next < n && next < com + LOOK && next < vload(sh.filled);
                     if (rd || fresh) {
                         // the counts after `com` commits (the ring entry stays
@@ -1153,16 +1153,19 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                         for (int q = 0; q < a.S; ++q) tc.ns[p][q] = sh.ns_ring[(com) & (kRS - 1)][q];
                         __threadfence_block();
                         if (vload(sh.committed) < com + kRS - 1) {
+                            // a re-evaluation goes to the first team free to
+                            // take it, ahead of the team's new move
+                            if (rd && atomicCAS(&redo, rd, 0) == rd) {
+                                mm = rd - 1;
+                            } else if (fresh) {
+                                mm = next;
+                                next += NTEAM;
+                            } else {
+                                continue;
+                            }
                             c0 = com;
                             acc0 = acc_seen;
                             go = 1;
-                            if (rd) {
-                                vstore(redo[team], 0);
-                                mm = rd - 1;
-                            } else {
-                                mm = next;
-                                next += NTEAM;
-                            }
                             break;
                         }
                         continue;
@@ -1346,7 +1349,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         for (int m = 0; m < n; ++m) {
             const unsigned long long tm0 = clock64();
             Slot &S = sh.slots[(m) & (kRS - 1)];
-            const int team = m % NTEAM;
             bool ok = true;
             if (m == a.stall_at) {
                 // diagnostic: a bounded wait on a flag nothing sets runs out,
@@ -1453,7 +1455,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 if (lane == 0) {
                     vstore(S.tag, 0);
                     __threadfence_block();
-                    vstore(redo[team], m + 1);
+                    vstore(redo, m + 1);
                 }
                 __syncwarp();
             }

@@ -64,7 +64,7 @@ FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one full-size chain launch (64 chains x 10^5
 # moves) from an ncu capture (profiles/k_chain_isotherm_fp32.md), valid for
 # the chain kernel source with this sha256 prefix only
-CHAIN_TRAFFIC = {"sha256_prefix": "23b4267a6c783ce0", "bytes": 19.18e6, "moves": 6.4e6}
+CHAIN_TRAFFIC = {"sha256_prefix": "7e1a83992c7c23cf", "bytes": 19.20e6, "moves": 6.4e6}
 DEFAULT_MOVES = {"isotherm": 100_000, "c2": 1_000_000, "c1": 10_000}
 DEFAULT_CPU_MOVES = {"isotherm": 20_000, "c2": 1_000_000, "c1": 10_000}
 

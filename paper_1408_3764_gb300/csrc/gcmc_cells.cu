@@ -4,9 +4,11 @@
 //
 // Build pipeline (all integer, deterministic):
 //   1. k_prepare       quantise positions, cell id per particle, histogram
+//                      (each particle keeps its arrival slot in its cell)
 //   2. k_species_*     index of each particle within its species (input rank)
 //   3. k_scan_*        exclusive prefix sum of the cell counts -> cell_start
-//   4. k_place         scatter particle numbers into their cell's range
+//   4. k_place         scatter particle numbers into their cell's range at
+//                      their arrival slots
 //   5. k_sort_cells    one warp per cell sorts its range by input index and
 //                      writes the compact and padded cell-major layouts
 #include <algorithm>
@@ -21,33 +23,27 @@ constexpr int kScanBlock = 1024;
 
 __global__ void k_prepare(const double *__restrict__ pos, const int32_t *__restrict__ species,
                           int64_t n, double q, int T, int S, uint4 *__restrict__ grid,
-                          int32_t *__restrict__ cellid, int32_t *__restrict__ count,
-                          int *__restrict__ status)
+                          int32_t *__restrict__ cellid, int32_t *__restrict__ cslot,
+                          int32_t *__restrict__ count, int *__restrict__ status)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int s = species[p];
         bool ok = (s >= 0 && s < S);
-        uint32_t X[3] = {0u, 0u, 0u};
+        uint32_t X[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double t = pos[3 * p + a] * q;
-            if (!(t == t) || t > 4.0e18 || t < -4.0e18) {
-                ok = false;
-            } else {
-                X[a] = (uint32_t)(unsigned long long)(long long)floor(t);
-            }
-        }
+        for (int a = 0; a < 3; ++a) X[a] = quantize_axis(pos[3 * p + a], q, ok);
         if (!ok) {
             atomicOr(status, kStatusBadInput);
             grid[p] = make_uint4(0u, 0u, 0u, 0u);
             cellid[p] = 0;
+            cslot[p] = 0;
             continue;
         }
         const int c = cell_of(X[0], X[1], X[2], T);
         grid[p] = make_uint4(X[0], X[1], X[2], (uint32_t)s);
         cellid[p] = c;
-        atomicAdd(&count[c], 1);
+        cslot[p] = atomicAdd(&count[c], 1);  // arrival slot; the order is fixed by k_sort_cells
     }
 }
 
@@ -197,15 +193,12 @@ __global__ void k_species_rank(const uint4 *__restrict__ grid, int64_t n, int S,
 }
 
 // ---- placement and per-cell stable ordering
-__global__ void k_place(const int32_t *__restrict__ cellid, int64_t n, const int32_t *__restrict__ start,
-                        int32_t *__restrict__ fill, int32_t *__restrict__ tmp)
+__global__ void k_place(const int32_t *__restrict__ cellid, const int32_t *__restrict__ cslot, int64_t n,
+                        const int32_t *__restrict__ start, int32_t *__restrict__ tmp)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cellid[p];
-        const int k = atomicAdd(&fill[c], 1);
-        tmp[start[c] + k] = (int32_t)p;
-    }
+         p += (int64_t)gridDim.x * blockDim.x)
+        tmp[start[cellid[p]] + cslot[p]] = (int32_t)p;
 }
 
 __global__ void k_sort_cells(const int32_t *__restrict__ tmp, const int32_t *__restrict__ start,
@@ -298,7 +291,7 @@ gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species
     const size_t o_cell = take((size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
     const size_t o_sidx = take((size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
     const size_t o_tmp = take((size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
-    const size_t o_fill = take((size_t)ncell * sizeof(int32_t));
+    const size_t o_slot = take((size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
     const size_t o_bc = take((size_t)(S * std::max<int64_t>(nb, 1)) * sizeof(int32_t));
     const size_t o_part = take((size_t)(nbc + 1) * sizeof(int32_t));
     const size_t o_small = take(64 * sizeof(int64_t));
@@ -317,8 +310,9 @@ gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species
     GCMC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
     GCMC_CUDA(ctx, cudaMemsetAsync(small, 0, 64 * sizeof(int64_t), st));
     if (n > 0) {
-        k_prepare<<<grid_for(ctx, n, 256), 256, 0, st>>>(pos, species, n, ctx->q, ctx->T, S, grid,
-                                                       cellid, ctx->cell_count, ctx->d_status);
+        k_prepare<<<grid_for(ctx, n, 256), 256, 0, st>>>(pos, species, n, ctx->q, ctx->T, S, grid, cellid,
+                                                       (int32_t *)(base + o_slot), ctx->cell_count,
+                                                       ctx->d_status);
         k_species_count<<<(unsigned)nb, kScanBlock, 0, st>>>(grid, n, S, bc, nb);
         k_species_scan<<<S, kScanBlock, 0, st>>>(bc, nb, small);
         k_species_rank<<<(unsigned)nb, kScanBlock, 0, st>>>(grid, n, S, bc, nb, sidx);
@@ -337,7 +331,7 @@ gcmc_status build_begin(gcmc_ctx *ctx, const double *pos, const int32_t *species
     ctx->pend_off[1] = o_cell;
     ctx->pend_off[2] = o_sidx;
     ctx->pend_off[3] = o_tmp;
-    ctx->pend_off[4] = o_fill;
+    ctx->pend_off[4] = o_slot;
     ctx->pend_off[5] = o_small;
     ctx->built = false;
     ctx->compact_valid = false;
@@ -364,7 +358,7 @@ gcmc_status build_finish(gcmc_ctx *ctx)
     int32_t *cellid = (int32_t *)(base + ctx->pend_off[1]);
     int32_t *sidx = (int32_t *)(base + ctx->pend_off[2]);
     int32_t *tmp = (int32_t *)(base + ctx->pend_off[3]);
-    int32_t *fill = (int32_t *)(base + ctx->pend_off[4]);
+    int32_t *cslot = (int32_t *)(base + ctx->pend_off[4]);
     int64_t *small = (int64_t *)(base + ctx->pend_off[5]);
     (void)grid;
     int64_t hsmall[9];
@@ -413,8 +407,7 @@ gcmc_status build_finish(gcmc_ctx *ctx)
         ctx->cpos_len = want;
     }
     if (n > 0) {
-        GCMC_CUDA(ctx, cudaMemsetAsync(fill, 0, ncell * sizeof(int32_t), st));
-        k_place<<<grid_for(ctx, n, 256), 256, 0, st>>>(cellid, n, ctx->cell_start, fill, tmp);
+        k_place<<<grid_for(ctx, n, 256), 256, 0, st>>>(cellid, cslot, n, ctx->cell_start, tmp);
         k_sort_cells<<<grid_for(ctx, ncell * 32, 256), 256, 0, st>>>(
             tmp, ctx->cell_start, ctx->cell_count, ncell, grid, sidx, cap, maxN, ctx->order, ctx->cpos,
             ctx->cell_pos, ctx->pos_by_id);

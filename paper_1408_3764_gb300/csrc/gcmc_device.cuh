@@ -57,6 +57,22 @@ __device__ __forceinline__ double uniform53(uint32_t w6, uint32_t w7)
 // ---------------------------------------------------------------------------
 // Grid and cells
 // ---------------------------------------------------------------------------
+// The grid coordinate of x (Sec. 3.2.1's binning on the 2^32 grid):
+// floor(x q) wrapped to 32 bits.  ok turns false when x q is not finite or
+// |x q| > 4e18.  One FP64 multiply and one conversion that rounds down (the
+// FP64 pipe is narrow on this part); the range test compares the magnitude's
+// bit pattern, which orders like the value.
+__device__ __forceinline__ uint32_t quantize_axis(double x, double q, bool &ok)
+{
+    const double t = x * q;
+    const unsigned long long mag = (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffull;
+    if (mag > 0x43cbc16d674ec800ull) {  // the bits of 4e18; NaN and infinities are above
+        ok = false;
+        return 0u;
+    }
+    return (uint32_t)(unsigned long long)__double2ll_rd(t);
+}
+
 // floor(X * T / 2^32): the cell coordinate of grid coordinate X.
 __device__ __forceinline__ int cell_coord(uint32_t X, uint32_t T) { return (int)__umulhi(X, T); }
 

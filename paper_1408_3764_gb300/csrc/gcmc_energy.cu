@@ -72,15 +72,6 @@ __device__ __forceinline__ void pair_acc(const uint4 &p, const uint4 &q, uint32_
     }
 }
 
-__device__ __forceinline__ uint32_t quantize_dev(double x, double q, bool &ok)
-{
-    const double t = x * q;
-    if (!(t == t) || t > 4.0e18 || t < -4.0e18) {
-        ok = false;
-        return 0u;
-    }
-    return (uint32_t)(unsigned long long)(long long)floor(t);
-}
 
 // ---------------------------------------------------------------------------
 // Neighbourhood kernels.  One CTA per cell: the cell's neighbourhood (the 27
@@ -386,7 +377,7 @@ __global__ void k_trial_bin(const double *__restrict__ pos, const int32_t *__res
         bool ok = s >= 0 && s < S;
         uint32_t X[3] = {0u, 0u, 0u};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) X[a] = quantize_dev(pos[3 * k + a], q, ok);
+        for (int a = 0; a < 3; ++a) X[a] = quantize_axis(pos[3 * k + a], q, ok);
         if (!ok) {
             atomicOr(status, kStatusBadInput);
             out[k] = __longlong_as_double(0x7ff8000000000000ll);

@@ -88,6 +88,33 @@ def test_build_rejects_bad_input():
         b.build_cells(torch.tensor([[1.0, 1.0, 2.0]]), torch.tensor([3]))
 
 
+def test_build_quantisation_edges_match_the_oracle():
+    """Grid quantisation at its edges: negative coordinates and coordinates
+    beyond the box wrap as the oracle's floor(x 2^32 / L) mod 2^32 does, and
+    both reject the same values (non-finite, |x 2^32 / L| > 4e18)."""
+    L = 10.0
+    q = 2.0 ** 32 / L
+    lim = 4.0e18 / q
+    xs = [0.0, -0.0, 1e-300, -1e-300, L, -L, 2.5 * L, -7.25 * L, np.nextafter(L, 0.0),
+          np.nextafter(0.0, -1.0), 123456.789, -98765.4321, lim, -lim, np.nextafter(lim, 0.0),
+          np.nextafter(lim, np.inf), np.nextafter(-lim, -np.inf), float("inf"), float("-inf"), float("nan")]
+    b = Box(L, 2.5, [[1.0]], [[1.0]])
+    for x in xs:
+        try:
+            want = O.quantize(x, L)
+        except ValueError:
+            want = None
+        p = torch.tensor([[x, 1.0, 2.0]], dtype=torch.float64)
+        if want is None:
+            with pytest.raises(RuntimeError):
+                b.build_cells(p, torch.tensor([0], dtype=torch.int32))
+        else:
+            b.build_cells(p, torch.tensor([0], dtype=torch.int32))
+            got = b.get_state()[1]
+            assert int(got[0, 0]) == want, x
+            assert int(got[0, 1]) == O.quantize(1.0, L) and int(got[0, 2]) == O.quantize(2.0, L)
+
+
 # -------------------------------------------------------- trial energies ---
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -544,22 +544,50 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_cell_energy(const uint4 *__re
 
 // Deterministic sum of n partials (one block); out[j] for j < width sums
 // partial[i * width + j].
-__global__ void k_sum_partials(const double *__restrict__ partial, int64_t n, int width,
-                               double *__restrict__ out)
+// Column sums of partial[n][width] (per-cell partial sums) in a fixed
+// order, in two launches: block b of k_sum_rows sums the rows
+// [b n / B, (b + 1) n / B) of every column (each thread a strided share, then
+// a fixed tree), and k_sum_blocks adds the B block sums of each column in
+// block order.  The result does not depend on timing.
+constexpr int kSumBlocks = 128;  // row blocks, at most
+constexpr int kSumThreads = 256;
+
+__global__ void __launch_bounds__(kSumThreads) k_sum_rows(const double *__restrict__ partial, int64_t n, int width,
+                                                          double *__restrict__ blk)
 {
-    __shared__ double sh[1024];
+    __shared__ double sh[kSumThreads];
+    const int t = threadIdx.x;
+    const int64_t r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
     for (int j = 0; j < width; ++j) {
         double s = 0.0;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partial[i * width + j];
-        sh[threadIdx.x] = s;
+        for (int64_t i = r0 + t; i < r1; i += kSumThreads) s += partial[i * width + j];
+        sh[t] = s;
         __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+            if (t < o) sh[t] += sh[t + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) out[j] = sh[0];
+        if (t == 0) blk[(int64_t)blockIdx.x * width + j] = sh[0];
         __syncthreads();
     }
+}
+
+__global__ void k_sum_blocks(const double *__restrict__ blk, int nb, int width, double *__restrict__ out)
+{
+    for (int j = threadIdx.x; j < width; j += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += blk[(int64_t)b * width + j];
+        out[j] = s;
+    }
+}
+
+// Launches the two column-sum kernels; blk holds kSumBlocks x width doubles.
+static void sum_partials(gcmc_ctx *ctx, const double *partial, int64_t n, int width, double *blk, double *out)
+{
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (n + kSumThreads - 1) / kSumThreads));
+    k_sum_rows<<<nb, kSumThreads, 0, ctx->stream>>>(partial, n, width, blk);
+    k_sum_blocks<<<1, 128, 0, ctx->stream>>>(blk, nb, width, out);
+    ctx->launches += 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -942,7 +970,7 @@ gcmc_status total_energy_begin(gcmc_ctx *ctx, bool virial_only)
 {
     gcmc_status st = make_compact(ctx);
     if (st != GCMC_OK) return st;
-    st = ensure_red(ctx, 2 * (size_t)ctx->ncell + 8);
+    st = ensure_red(ctx, 2 * (size_t)ctx->ncell + 8 + 2 * kSumBlocks);
     if (st != GCMC_OK) return st;
     st = ensure_pinned(ctx, kPinnedBytes);
     if (st != GCMC_OK) return st;
@@ -964,8 +992,8 @@ gcmc_status total_energy_begin(gcmc_ctx *ctx, bool virial_only)
             ctx->cpos, ctx->cell_start, ctx->T, ctx->ncell, ctx->R2, r2lo, r2hi, wrap, ctx->ff, ctx->fd, ctx->d_red,
             ctx->d_status);
     }
-    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(ctx->d_red, ctx->ncell, 2, ctx->d_red + 2 * ctx->ncell);
-    ctx->launches += 2;
+    sum_partials(ctx, ctx->d_red, ctx->ncell, 2, ctx->d_red + 2 * ctx->ncell + 8, ctx->d_red + 2 * ctx->ncell);
+    ctx->launches += 1;
     GCMC_CUDA(ctx, cudaGetLastError());
     double *hp = (double *)ctx->h_pinned;
     const double *dsum = ctx->d_red + 2 * ctx->ncell;
@@ -1013,7 +1041,7 @@ gcmc_status energy_grad_begin(gcmc_ctx *ctx, float *dpos)
     if (st != GCMC_OK) return st;
     const int S = ctx->S;
     const int width = 2 + 2 * S * S;
-    st = ensure_red(ctx, (size_t)ctx->ncell * width + width);
+    st = ensure_red(ctx, (size_t)ctx->ncell * width + width + (size_t)kSumBlocks * width);
     if (st != GCMC_OK) return st;
     st = ensure_pinned(ctx, kPinnedBytes);
     if (st != GCMC_OK) return st;
@@ -1042,8 +1070,8 @@ gcmc_status energy_grad_begin(gcmc_ctx *ctx, float *dpos)
         else GCMC_GRAD(false, kMaxSpecies);
     }
 #undef GCMC_GRAD
-    k_sum_partials<<<1, 1024, 0, ctx->stream>>>(part, ctx->ncell, width, res);
-    ctx->launches += 2;
+    sum_partials(ctx, part, ctx->ncell, width, res + width, res);
+    ctx->launches += 1;
     GCMC_CUDA(ctx, cudaGetLastError());
     double *hp = (double *)ctx->h_pinned + 16;
     GCMC_CUDA(ctx, cudaMemcpyAsync(hp, res, width * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

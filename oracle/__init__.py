@@ -69,6 +69,8 @@ def lib():
         L.orc_get_virial.argtypes = [vp]
         L.orc_get_virial.restype = d
         L.orc_move_words.argtypes = [u64, u64, u32, vp]
+        L.orc_pick_index.argtypes = [i64, vp, C.c_int]
+        L.orc_pick_index.restype = i64
         L.orc_run_moves.argtypes = [vp, u64, u32, u64, i64, vp, d, vp, vp]
         L.orc_run_moves.restype = C.c_int
         L.orc_run_moves_ex.argtypes = [vp, u64, u32, u64, i64, vp, d, vp, vp, vp]
@@ -131,6 +133,14 @@ def move_words(seed: int, move: int, chain: int = 0) -> np.ndarray:
     out = np.zeros(8, dtype=np.uint32)
     lib().orc_move_words(seed, move, chain, _p(out))
     return out
+
+
+def pick_index(n: int, words, move_type: int) -> int:
+    """The index a displacement (move_type 0) or deletion (2) picks among n >= 1
+    candidates from the move's eight words."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    assert w.shape == (8,) and n >= 1
+    return int(lib().orc_pick_index(int(n), _p(w), int(move_type)))
 
 
 def lj(r2: float, eps: float, sigma: float):

@@ -773,16 +773,48 @@ void orc_move_words(uint64_t seed, uint64_t m, uint32_t chain, uint32_t w[8])
     orc_philox4x32_10(c1, key, w + 4);
 }
 
+/* The particle a displacement (type 0) or a deletion (type 2) takes among
+ * n >= 1 candidates.  Algorithm 1 takes one at random, uniformly; the paper
+ * does not say how the index is drawn.  Reading: with 2^k the smallest power
+ * of two that is at least n, the top k bits of independent words are tried
+ * in turn and the first value below n is the index (rejection sampling, so
+ * every index is equally likely).  A deletion tries w1, w2 and w3 (a
+ * deletion does not use w2-w4 otherwise); a displacement tries w1 and, when
+ * k <= 16, the top k bits of the low 16 bits of w1.  If no try is below n
+ * the index is floor(f n / 2^32) of one more word f, independent of the
+ * tries: w4 for a deletion, w5 for a displacement.  The index changes with
+ * n only when n passes a power of two, when a try lies between the two
+ * counts, or when every try fails. */
+int64_t orc_pick_index(int64_t n, const uint32_t w[8], int type)
+{
+    int k = 0;
+    while (((int64_t)1 << k) < n) ++k;
+    if (k == 0) return 0; /* a single candidate */
+    uint64_t tries[3];
+    int ntries = 0;
+    tries[ntries++] = (uint64_t)w[1] >> (32 - k);
+    if (type == 2) {
+        tries[ntries++] = (uint64_t)w[2] >> (32 - k);
+        tries[ntries++] = (uint64_t)w[3] >> (32 - k);
+    } else if (k <= 16) {
+        tries[ntries++] = (uint64_t)(w[1] & 0xFFFFu) >> (16 - k);
+    }
+    for (int j = 0; j < ntries; ++j)
+        if ((int64_t)tries[j] < n) return (int64_t)tries[j];
+    uint32_t f = (type == 2) ? w[4] : w[5];
+    return (int64_t)(((uint64_t)f * (uint64_t)n) >> 32);
+}
+
 /* Runs moves [first, first + n_moves) of the chain.  Per move (Algorithm 1
  * with the acceptance rules of Eqs. 3-5, read with the textbook sign of
  * the chemical potential):
  *   w0 picks the move type against thresholds floor(p * 2^32);
- *   displacement: particle k = (w1 * N) >> 32 over all species in
+ *   displacement: particle k = orc_pick_index(N, w, 0) over all species in
  *     species-major order, each axis moves by ((w * (2D+1)) >> 32) - D grid
  *     units (D = the half-width in grid units), ln A = -beta dU;
  *   insertion: species (w5 * S) >> 32, grid position (w2, w3, w4),
  *     ln A = ln z_s + ln V - ln(N_s + 1) - beta dU;
- *   deletion: species (w5 * S) >> 32, index (w1 * N_s) >> 32,
+ *   deletion: species (w5 * S) >> 32, index orc_pick_index(N_s, w, 2),
  *     ln A = ln N_s - ln z_s - ln V - beta dU (rejected when N_s = 0);
  *   u = ((w6 >> 5) * 2^26 + (w7 >> 6)) * 2^-53, accept iff ln u < ln A.
  * The cell list follows Sec. 3.2.5 (swap-with-last removal, append);
@@ -832,7 +864,7 @@ int orc_run_moves_ex(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first
             if (N == 0) {
                 possible = 0;
             } else {
-                int64_t k = (int64_t)(((uint64_t)w[1] * (uint64_t)N) >> 32);
+                int64_t k = orc_pick_index(N, w, 0);
                 s = 0;
                 while (k >= sys->n[s]) {
                     k -= sys->n[s];
@@ -866,7 +898,7 @@ int orc_run_moves_ex(orc_sys *sys, uint64_t seed, uint32_t chain, uint64_t first
             if (sys->n[s] == 0) {
                 possible = 0;
             } else {
-                i = (int64_t)(((uint64_t)w[1] * (uint64_t)sys->n[s]) >> 32);
+                i = orc_pick_index(sys->n[s], w, 2);
                 double w0 = 0.0;
                 dU = -energy_cells_w(sys, &sys->pos[s][3 * i], s, s, i, &uabs, &w0, &sabs);
                 dW = -w0;

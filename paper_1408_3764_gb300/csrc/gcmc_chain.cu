@@ -338,6 +338,24 @@ struct Chain {
         return sh.words[(first_mod + m) & (kRW - 1)];
     }
 
+    // Whether move m's trial is the same for every count its pick can meet
+    // at its turn, `delta` moves after the counts ns[] (each pending move
+    // changes one count by at most one): then the evaluation needs no count
+    // prediction.  An insertion does not depend on the counts; a
+    // displacement among several species does through the species of the
+    // pick, and is left to the prediction.
+    __device__ __forceinline__ bool pick_settled(int m, const int *ns, int delta) const
+    {
+        const WordRec &W = words(m);
+        const uint32_t w0 = W.w[0];
+        const int type = (w0 < a.thr_disp) ? 0 : ((w0 < a.thr_ins) ? 1 : 2);
+        if (type == 1) return true;
+        if (type == 0 && a.S != 1) return false;
+        const int n = ns[type == 2 ? (int)__umulhi(W.w[5], (uint32_t)a.S) : 0];
+        if (n - delta < 1) return false;
+        return pick_is_stable((uint32_t)(n - delta), (uint32_t)(n + delta), W.w, type);
+    }
+
     // the trial of move m given the particle counts ns[] (warp-uniform)
     __device__ __forceinline__ Trial make_trial(int m, const int *ns) const
     {
@@ -357,7 +375,7 @@ struct Chain {
             if (N == 0) {
                 t.possible = 0;
             } else {
-                int k = (int)__umulhi(W.w[1], (uint32_t)N);
+                int k = pick_index((uint32_t)N, W.w, 0);
                 while (k >= ns[s]) {
                     k -= ns[s];
                     ++s;
@@ -368,7 +386,7 @@ struct Chain {
             s = (int)__umulhi(W.w[5], (uint32_t)a.S);
             if (type == 2) {
                 if (ns[s] == 0) t.possible = 0;
-                else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
+                else idx = pick_index((uint32_t)ns[s], W.w, 2);
             }
         }
         t.s = s;
@@ -1000,7 +1018,7 @@ __device__ __forceinline__ bool pick_ok(const Chain<F32, VIR> &C, const Shared &
         if (N == 0) {
             possible = 0;
         } else {
-            int k = (int)__umulhi(W.w[1], (uint32_t)N);
+            int k = pick_index((uint32_t)N, W.w, 0);
             while (k >= ns[s]) {
                 k -= ns[s];
                 ++s;
@@ -1010,7 +1028,7 @@ __device__ __forceinline__ bool pick_ok(const Chain<F32, VIR> &C, const Shared &
     } else {
         s = (int)t.s;
         if (ns[s] == 0) possible = 0;
-        else idx = (int)__umulhi(W.w[1], (uint32_t)ns[s]);
+        else idx = pick_index((uint32_t)ns[s], W.w, 2);
     }
     if (possible != (int)t.possible) return false;
     if (possible && (s != (int)t.s || idx != t.idx)) return false;
@@ -1208,9 +1226,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 // +1 or -1 for its species; one not yet evaluated counts as
                 // the chain's more frequent outcome for its kind.  The
                 // particle pick uses the prediction; the committer checks the
-                // pick against the actual counts.
+                // pick against the actual counts.  Skipped when the pick is
+                // the same for every count the pending moves can leave.
                 const int go = tc.go[p], mm = tc.m[p], c0 = tc.c0[p];
-                if (go == 1 && mm > c0) {
+                if (go == 1 && mm > c0 && !C.pick_settled(mm, tc.ns[p], mm - c0)) {
                     const int k = c0 + lane;
                     int d = 0, sk = 0;
                     if (k < mm) {
@@ -1410,9 +1429,9 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 const int *ring = sh.ns_ring[m & (kRS - 1)];
                 bool pick = c0 == m || tcur.type == 1;
                 if (!pick && (tcur.type == 2 || a.S == 1)) {
-                    // one count decides the pick: idx = floor(w1 n / 2^32)
+                    // one count decides the pick
                     const int na = ring[tcur.type == 2 ? (int)tcur.s : 0];
-                    pick = tcur.possible ? (na > 0 && (int)__umulhi(C.words(m).w[1], (uint32_t)na) == tcur.idx)
+                    pick = tcur.possible ? (na > 0 && pick_index((uint32_t)na, C.words(m).w, tcur.type) == tcur.idx)
                                          : na == 0;
                 } else if (!pick) {
                     pick = __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == ring[lane]) || pick_ok(C, sh, tcur, m);
@@ -1725,19 +1744,22 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
 }
 
 // ---------------------------------------------------------------- host side
-// Team shapes the launcher can use: (warps per team, teams).  More teams
-// evaluate more moves ahead (better when moves rarely conflict); larger
-// teams evaluate one move faster (better when N changes often).
+// Team shapes the launcher can use: (warps per team, teams, look-ahead).
+// More teams evaluate more moves ahead (better when moves rarely conflict);
+// larger teams evaluate one move faster (better when N changes often).
+// Shape 0 leaves the committer's SM sub-partition to the committer and the
+// keeper (twelve evaluator warps on the other three); shape 1 adds two
+// evaluator warps there.
 constexpr int kNumConfigs = 4;
 
 template <bool F32, bool VIR>
 static void *chain_kernel(int config)
 {
     switch (config) {
-    case 1: return (void *)k_chain<F32, VIR, 4, 3, 6, 2>;
-    case 2: return (void *)k_chain<F32, VIR, 3, 4, 8, 2>;
-    case 3: return (void *)k_chain<F32, VIR, 2, 6, 12, 3>;
-    default: return (void *)k_chain<F32, VIR, 7, 2, 4, 2>;
+    case 1: return (void *)k_chain<F32, VIR, 7, 2, 4, 2>;
+    case 2: return (void *)k_chain<F32, VIR, 4, 3, 6, 2>;
+    case 3: return (void *)k_chain<F32, VIR, 3, 4, 8, 2>;
+    default: return (void *)k_chain<F32, VIR, 6, 2, 4, 2>;
     }
 }
 

@@ -54,6 +54,67 @@ __device__ __forceinline__ double uniform53(uint32_t w6, uint32_t w7)
     return (double)k * 1.1102230246251565404e-16;  // 2^-53
 }
 
+// The index a displacement (type 0) or a deletion (type 2) picks among n >= 1
+// candidates (Algorithm 1's uniform choice): 2^k the smallest power of two at
+// least n, the top k bits of the tries -- w[1], w[2], w[3] for a deletion;
+// w[1] and, for k <= 16, the top k bits of w[1]'s low half for a
+// displacement -- and the first one below n wins (rejection sampling);
+// when none does, floor(f n / 2^32) of f = w[4] (deletion) or w[5]
+// (displacement), words independent of the tries.  The index moves with n
+// only when n passes a power of two, when a try lies between the two
+// counts, or when every try fails, so a speculative evaluation that guessed
+// the count slightly wrong usually picked the right particle all the same.
+__device__ __forceinline__ int pick_index(uint32_t n, const uint32_t *w, int type)
+{
+    const int k = 32 - __clz((int)(n - 1u));  // n = 1: clz(0) = 32, k = 0
+    if (k == 0) return 0;
+    const int sh = 32 - k;
+    uint32_t d = w[1] >> sh;
+    if (d < n) return (int)d;
+    if (type == 2) {
+        d = w[2] >> sh;
+        if (d < n) return (int)d;
+        d = w[3] >> sh;
+        if (d < n) return (int)d;
+        return (int)__umulhi(w[4], n);
+    }
+    if (k <= 16) {
+        d = (w[1] << 16) >> sh;
+        if (d < n) return (int)d;
+    }
+    return (int)__umulhi(w[5], n);
+}
+
+// Whether pick_index gives the same index for every count in [lo, hi]
+// (1 <= lo <= hi): the counts share k, and a try below lo comes before any
+// try in [lo, hi).
+__device__ __forceinline__ bool pick_is_stable(uint32_t lo, uint32_t hi, const uint32_t *w, int type)
+{
+    const int k = 32 - __clz((int)(hi - 1u));
+    if (32 - __clz((int)(lo - 1u)) != k) return false;
+    if (k == 0) return true;
+    const int sh = 32 - k;
+    uint32_t tries[3];
+    int nt = 1;
+    tries[0] = w[1] >> sh;
+    if (type == 2) {
+        tries[1] = w[2] >> sh;
+        tries[2] = w[3] >> sh;
+        nt = 3;
+    } else if (k <= 16) {
+        tries[1] = (w[1] << 16) >> sh;
+        nt = 2;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < nt) {
+            if (tries[j] < lo) return true;
+            if (tries[j] < hi) return false;
+        }
+    }
+    return false;  // every try fails for some count: the fallback depends on it
+}
+
 // ---------------------------------------------------------------------------
 // Grid and cells
 // ---------------------------------------------------------------------------

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArg
             if (N == 0) {
                 t.possible = 0;
             } else {
-                long long k = (long long)__umulhi(W.w[1], (uint32_t)N);
+                long long k = pick_index((uint32_t)N, W.w, 0);
                 while (k >= sh.n[t.s]) {
                     k -= sh.n[t.s];
                     ++t.s;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kMicroThreads, 1) k_micro_chain(const MicroArg
             t.s = (int)__umulhi(W.w[5], (uint32_t)a.S);
             if (t.type == 2) {
                 if (sh.n[t.s] == 0) t.possible = 0;
-                else t.idx = (long long)__umulhi(W.w[1], (uint32_t)sh.n[t.s]);
+                else t.idx = pick_index((uint32_t)sh.n[t.s], W.w, 2);
             }
         }
         const long long ns = sh.n[t.s];

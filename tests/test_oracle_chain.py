@@ -344,3 +344,95 @@ def test_sum_abs_u_matches_textbook_brute_force():
         want = np.abs(4 * eps[0, 0] * (sr6 * sr6 - sr6)).sum()
         assert sabs[m] == pytest.approx(want, rel=1e-9, abs=1e-12)
         assert abs(tr["dU"][m]) <= sabs[m] * (1 + 1e-12)
+
+
+# ---- the particle pick (Algorithm 1: a particle chosen uniformly at random)
+def _words(**kv):
+    w = np.zeros(8, np.uint32)
+    for k, v in kv.items():
+        w[int(k[1:])] = v
+    return w
+
+
+def test_pick_index_worked_cases():
+    """Values worked out by hand from the rule: 2^k the smallest power of two
+    >= n, the top k bits of the tries (deletion: w1, w2, w3; displacement: w1,
+    then the top k bits of w1's low half when k <= 16), the first below n
+    wins, else floor(f n / 2^32) with f = w4 (deletion) or w5 (displacement)."""
+    full = 0xFFFFFFFF
+    assert O.pick_index(1, _words(w1=full, w2=full, w3=full, w4=full, w5=full), 2) == 0
+    assert O.pick_index(1, _words(w1=full, w5=full), 0) == 0
+    # n = 5, k = 3: 0x6... -> top three bits 011 = 3
+    assert O.pick_index(5, _words(w1=0x60000000), 2) == 3
+    assert O.pick_index(5, _words(w1=0x60000000), 0) == 3
+    # first try 7 >= 5, the second (w2 = 0x2...: 001) wins
+    assert O.pick_index(5, _words(w1=0xE0000000, w2=0x20000000), 2) == 1
+    # displacement: 7 >= 5, then w1's low half 0x4000 -> top three bits 010 = 2
+    assert O.pick_index(5, _words(w1=0xE0004000), 0) == 2
+    # every try fails: floor(2^31 * 5 / 2^32) = 2 from w4; floor(3 * 2^30 * 5 / 2^32) = 3 from w5
+    assert O.pick_index(5, _words(w1=full, w2=full, w3=full, w4=0x80000000, w5=0), 2) == 2
+    assert O.pick_index(5, _words(w1=full, w4=0, w5=0xC0000000), 0) == 3
+    # n a power of two: the first try always wins
+    assert O.pick_index(8, _words(w1=full), 2) == 7
+    assert O.pick_index(8, _words(w1=full), 0) == 7
+    # n = 70,000, k = 17 > 16: one try (0x8000 >> 15 = 1), else w5 (2^30 * 70000 / 2^32 = 17500)
+    assert O.pick_index(70_000, _words(w1=0x8000), 0) == 1
+    assert O.pick_index(70_000, _words(w1=full, w5=0x40000000), 0) == 17_500
+    assert O.pick_index(70_000, _words(w1=full, w2=0x8000, w3=full, w4=full), 2) == 1
+
+
+@pytest.mark.parametrize("n,bins", [(3, 3), (5, 5), (100, 10), (1000, 20), (70_000, 20)])
+@pytest.mark.parametrize("move_type", [0, 2])
+def test_pick_index_is_uniform(n, bins, move_type):
+    """Over random words every index is equally likely: a chi-square test on
+    `bins` equal groups of indices (p = 1e-4).  Taking the tries modulo n, or
+    a fallback word that is not independent of the failed tries, piles the
+    picks onto some indices and fails it."""
+    rng = np.random.default_rng(n * 7 + move_type)
+    draws = 40_000
+    words = rng.integers(0, 1 << 32, size=(draws, 8), dtype=np.uint64).astype(np.uint32)
+    idx = np.array([O.pick_index(n, w, move_type) for w in words])
+    assert idx.min() >= 0 and idx.max() < n
+    group = idx * bins // n
+    h = np.bincount(group, minlength=bins)
+    sizes = np.bincount(np.arange(n) * bins // n, minlength=bins)
+    expect = draws * sizes / n
+    chi2 = ((h - expect) ** 2 / expect).sum()
+    limit = {2: 18.4, 4: 23.5, 9: 33.7, 19: 47.2}[bins - 1]
+    assert chi2 < limit, (n, move_type, h)
+
+
+@pytest.mark.parametrize("move_type,limit", [(2, 0.04), (0, 0.08)])
+def test_pick_index_barely_depends_on_the_count(move_type, limit):
+    """The reason for the rule: 700 and 701 candidates pick the same index
+    unless a try lands on 700 or every try fails (then the fallback's
+    floor(f n / 2^32) moves in about half the cases): about 2 % of deletions
+    and 5 % of displacements, where floor(w1 n / 2^32) would differ for about
+    half of them."""
+    rng = np.random.default_rng(700 + move_type)
+    words = rng.integers(0, 1 << 32, size=(20_000, 8), dtype=np.uint64).astype(np.uint32)
+    diff = np.mean([O.pick_index(700, w, move_type) != O.pick_index(701, w, move_type) for w in words])
+    assert diff < limit, diff
+
+
+def test_chain_picks_by_the_rule():
+    """Every displacement and deletion of an ideal-gas chain takes the index
+    the rule gives for its move's words and the count before the move."""
+    L = 9.0
+    s = O.System(L, 2.5, [[0.0]], [[1.0]])
+    n0 = 37
+    s.build(W.uniform_positions(n0, L, 8), np.zeros(n0, np.int32))
+    s.set_energy(0.0)
+    seed, n_moves = 29, 6000
+    tr, _ = s.run_moves(seed, 0, n_moves, 0.4, 0.3, 0.3, 0.3, 1.0, [math.log(4.0)])
+    n_after = _n_trajectory(tr, n0)
+    n_before = np.concatenate([[n0], n_after[:-1]])
+    checked = 0
+    for m in range(n_moves):
+        t = int(tr["type"][m])
+        if t == 1 or n_before[m] == 0:
+            continue
+        w = O.move_words(seed, m, 0)
+        assert int(tr["index"][m]) == O.pick_index(int(n_before[m]), w, t), m
+        checked += 1
+    assert checked > 3000

@@ -342,9 +342,17 @@ gcmc_status gcmc_chain_counters(gcmc_ctx *ctx, int64_t *refetched, int64_t *refi
  * leaders waiting for an eligible move and [6] the teams evaluating (summed
  * over teams), [7] evaluations; [8] .. [10] the parts of [1]: the count
  * epoch, the logged moves, the particle pick; [11] booking a decided move.
- * Zeros for the microcell chain.
+ * Zeros for the microcell chain, and for a run without the counters
+ * (gcmc_set_chain_profile).
  * Errors: INVALID_ARG. */
 gcmc_status gcmc_chain_profile(gcmc_ctx *ctx, double *cycles);
+
+/* Whether the chain runs of this context count the cycles gcmc_chain_profile
+ * reports (on = 1; 0, the default, leaves the clock reads out of the
+ * kernel, which runs about 2.5 % faster).  A batch counts them when any of
+ * its contexts asks.  No paper counterpart (a diagnostic).
+ * Errors: INVALID_ARG (NULL, on not 0 or 1). */
+gcmc_status gcmc_set_chain_profile(gcmc_ctx *ctx, int32_t on);
 
 /* Team shape of the chain kernel (how its warps split the evaluation of
  * upcoming moves): 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape

@@ -89,6 +89,7 @@ SIGNATURES = {
     "gcmc_kernel_launches": (C.c_int, [_vp, _vp]),
     "gcmc_chain_counters": (C.c_int, [_vp, _vp, _vp]),
     "gcmc_chain_profile": (C.c_int, [_vp, _vp]),
+    "gcmc_set_chain_profile": (C.c_int, [_vp, C.c_int32]),
     "gcmc_set_chain_config": (C.c_int, [_vp, C.c_int32]),
     "gcmc_get_chain_config": (C.c_int, [_vp, _vp]),
     "gcmc_batch_create": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),

@@ -184,6 +184,15 @@ struct WordRec {
 
 constexpr int kGMax = 8;  // warps per evaluation team, at most
 
+// SM clock for the per-role cycle counters of a profiled launch; an
+// unprofiled launch compiles the reads (and the sums) away.
+template <bool PROF>
+__device__ __forceinline__ unsigned long long prof_clock()
+{
+    if constexpr (PROF) return clock64();
+    else return 0ull;
+}
+
 struct Slot {  // evaluators -> committer, one per move in flight
     Trial t;                      // written by the team's warp 0
     uint4 last_val;               // the old cell's last entry (by the lane that met it)
@@ -1053,7 +1062,7 @@ struct TeamCtl {
 // committer finds invalid is evaluated again by the first team free to take
 // it, ahead of that team's new moves.  KU: slots per work cell a lane loads
 // at once.
-template <bool F32, bool VIR, int G, int NTEAM, int LOOK, int KU>
+template <bool F32, bool VIR, int G, int NTEAM, int LOOK, int KU, bool PROF>
 __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *__restrict__ args)
 {
     static_assert(G <= kGMax && LOOK < kRS && NTEAM <= 15, "team shape");
@@ -1150,7 +1159,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         for (int it = 0;; ++it) {
             const int p = it & 1;
             if (j == 0 && lane == 0) {
-                const unsigned long long ti = clock64();
+                const unsigned long long ti = prof_clock<PROF>();
                 Wait wt;
                 int go = 0, mm = 0, c0 = 0, acc0 = 0;
                 for (;;) {
@@ -1216,7 +1225,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 tc.m[p] = mm;
                 tc.c0[p] = c0;
                 __threadfence_block();
-                cyc_idle += clock64() - ti;
+                cyc_idle += prof_clock<PROF>() - ti;
             }
             __syncwarp();
             if (j == 0) {
@@ -1267,7 +1276,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 }
                 break;
             }
-            const unsigned long long te = clock64();
+            const unsigned long long te = prof_clock<PROF>();
             const int m = tc.m[p];
             const Trial t = C.make_trial(m, tc.ns[p]);
             Slot &S = sh.slots[(m) & (kRS - 1)];
@@ -1307,7 +1316,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 __threadfence_block();
                 last = atomicAdd(&S.arrive, 1) == G - 1;
                 if (j == 0) {
-                    cyc_eval += clock64() - te;
+                    cyc_eval += prof_clock<PROF>() - te;
                     ++n_eval;
                 }
             }
@@ -1366,7 +1375,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         unsigned long long cv_e = 0, cv_l = 0, cv_p = 0, cb = 0;
         int nacc = 0;  // moves accepted so far (the committer's count, published in sh.nacc)
         for (int m = 0; m < n; ++m) {
-            const unsigned long long tm0 = clock64();
+            const unsigned long long tm0 = prof_clock<PROF>();
             Slot &S = sh.slots[(m) & (kRS - 1)];
             bool ok = true;
             if (m == a.stall_at) {
@@ -1393,7 +1402,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             for (;; ++attempt) {
                 // wait for the trial of m (its evaluation under way) and for
                 // room in the keeper's book
-                const unsigned long long tw = clock64();
+                const unsigned long long tw = prof_clock<PROF>();
                 Wait wt;
                 for (;;) {
                     int r = 0;
@@ -1414,7 +1423,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                     }
                 }
                 if (!ok) break;
-                const unsigned long long tv = clock64();
+                const unsigned long long tv = prof_clock<PROF>();
                 cw += tv - tw;
                 __threadfence_block();
                 c0 = S.c0;
@@ -1436,9 +1445,9 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 } else if (!pick) {
                     pick = __all_sync(0xffffffffu, lane >= a.S || S.nsu[lane] == ring[lane]) || pick_ok(C, sh, tcur, m);
                 }
-                const unsigned long long tv1 = clock64();
+                const unsigned long long tv1 = prof_clock<PROF>();
                 const bool logs = !pick || c0 == m || quiet || logs_ok(C, sh, tcur, c0, m, lane);
-                const unsigned long long tv2 = clock64();
+                const unsigned long long tv2 = prof_clock<PROF>();
                 // then wait for the team's sums
                 Wait wa;
                 for (;;) {
@@ -1456,7 +1465,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                     }
                 }
                 if (!ok) break;
-                const unsigned long long tv3 = clock64();
+                const unsigned long long tv3 = prof_clock<PROF>();
                 cw += tv3 - tv2;
                 __threadfence_block();
                 // the team's warps must have read the counts of one epoch
@@ -1464,7 +1473,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 const int q0 = S.pseq[0];
                 const bool one_epoch = quiet || (__all_sync(0xffffffffu, lane >= G || S.pseq[lane] == q0) && q0 >= 0);
                 const bool valid = pick && (c0 == m || quiet || (one_epoch && logs));
-                const unsigned long long tv4 = clock64();
+                const unsigned long long tv4 = prof_clock<PROF>();
                 cv += (tv2 - tv) + (tv4 - tv3);
                 cv_p += tv1 - tv;
                 cv_l += tv2 - tv1;
@@ -1479,7 +1488,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 __syncwarp();
             }
             if (!ok) break;
-            const unsigned long long td = clock64();
+            const unsigned long long td = prof_clock<PROF>();
             const Trial t = tcur;
             const int self_slot = S.self_slot;
             const uint4 last_val = S.last_val;
@@ -1549,11 +1558,11 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 break;
             }
             LogRec &L = sh.logs[(m) & (kRS - 1)];
-            const unsigned long long tapp = clock64();
+            const unsigned long long tapp = prof_clock<PROF>();
             cd += tapp - td;
             if (fin & 1) C.apply(t, self_slot, last_val, L);
             else if (lane == 0) L.head.x = 0;
-            const unsigned long long tb0 = clock64();
+            const unsigned long long tb0 = prof_clock<PROF>();
             ca += tb0 - tapp;
             __syncwarp();
             if (lane < kMaxSpecies) sh.ns_ring[((m + 1)) & (kRS - 1)][lane] = (int)sh.n[lane];
@@ -1583,7 +1592,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             }
             nacc += fin & 1;
             __syncwarp();
-            const unsigned long long tend = clock64();
+            const unsigned long long tend = prof_clock<PROF>();
             cb += tend - tb0;
             ct += tend - tm0;
         }
@@ -1752,15 +1761,21 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
 // evaluator warps there.
 constexpr int kNumConfigs = 4;
 
-template <bool F32, bool VIR>
+template <bool F32, bool VIR, bool PROF>
 static void *chain_kernel(int config)
 {
     switch (config) {
-    case 1: return (void *)k_chain<F32, VIR, 7, 2, 4, 2>;
-    case 2: return (void *)k_chain<F32, VIR, 4, 3, 6, 2>;
-    case 3: return (void *)k_chain<F32, VIR, 3, 4, 8, 2>;
-    default: return (void *)k_chain<F32, VIR, 6, 2, 4, 2>;
+    case 1: return (void *)k_chain<F32, VIR, 7, 2, 4, 2, PROF>;
+    case 2: return (void *)k_chain<F32, VIR, 4, 3, 6, 2, PROF>;
+    case 3: return (void *)k_chain<F32, VIR, 3, 4, 8, 2, PROF>;
+    default: return (void *)k_chain<F32, VIR, 6, 2, 4, 2, PROF>;
     }
+}
+
+template <bool F32, bool VIR>
+static void *chain_kernel(int config, bool prof)
+{
+    return prof ? chain_kernel<F32, VIR, true>(config) : chain_kernel<F32, VIR, false>(config);
 }
 
 int chain_threads(int) { return kChainWarps * 32; }
@@ -1905,11 +1920,15 @@ static gcmc_status run_jobs(std::vector<ChainJob> &jobs, cudaStream_t st, bool f
     size_t smem = 16;
     for (auto &j : jobs) smem = std::max(smem, ((size_t)j.ctx->ncell * sizeof(uint16_t) + 15) / 16 * 16);
     if (f32) smem += kMaxEW * kQ * sizeof(int4);
-    // the virial sums are compiled in only when a chain of the launch keeps it
-    bool vir = false;
-    for (auto &j : jobs) vir |= (j.mix.flags & GCMC_MIX_VIRIAL) != 0;
-    void *kern = f32 ? (vir ? chain_kernel<true, true>(config) : chain_kernel<true, false>(config))
-                     : (vir ? chain_kernel<false, true>(config) : chain_kernel<false, false>(config));
+    // the virial sums are compiled in only when a chain of the launch keeps
+    // it, the cycle counters only when a chain's context asked for them
+    bool vir = false, prof = false;
+    for (auto &j : jobs) {
+        vir |= (j.mix.flags & GCMC_MIX_VIRIAL) != 0;
+        prof |= j.ctx->chain_prof;
+    }
+    void *kern = f32 ? (vir ? chain_kernel<true, true>(config, prof) : chain_kernel<true, false>(config, prof))
+                     : (vir ? chain_kernel<false, true>(config, prof) : chain_kernel<false, false>(config, prof));
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);

@@ -590,6 +590,13 @@ gcmc_status gcmc_set_chain_config(gcmc_ctx *ctx, int32_t config)
     return GCMC_OK;
 }
 
+gcmc_status gcmc_set_chain_profile(gcmc_ctx *ctx, int32_t on)
+{
+    if (!ctx || (on != 0 && on != 1)) return GCMC_ERR_INVALID_ARG;
+    ctx->chain_prof = on != 0;
+    return GCMC_OK;
+}
+
 gcmc_status gcmc_get_chain_config(gcmc_ctx *ctx, int32_t *config)
 {
     if (!ctx || !config) return GCMC_ERR_INVALID_ARG;

@@ -69,6 +69,7 @@ struct gcmc_ctx {
     int64_t last_refines = 0;
     double last_prof[12] = {};  // chain kernel cycle counters of the last run (ChainOut::prof)
     int chain_config = -1;  // team shape of the chain kernel (-1: tuned on the first call)
+    bool chain_prof = false;  // chain launches count cycles per role (gcmc_chain_profile)
     uint64_t wait_ns = 0;   // limit of the chain kernel's waits (0: the default, 1 s)
     int64_t stall_at = -1;  // diagnostic stall of the committer at this move of a call (-1 none)
 

@@ -178,9 +178,15 @@ class Box:
                                             out[1:].ctypes.data_as(C.c_void_p)), self._h)
         return dict(refetched=int(out[0]), refined=int(out[1]))
 
+    def set_chain_profile(self, on: bool = True):
+        """Whether the following chain runs count cycles per role (chain_profile); off by default,
+        since the clock reads slow the kernel by about 2.5 %."""
+        check(self._lib.gcmc_set_chain_profile(self._h, 1 if on else 0), self._h)
+
     def chain_profile(self) -> dict:
-        """SM cycles of the last chain run by role: committer waiting, validity, decision,
-        applying, loop total; team leaders idle, teams evaluating, evaluations."""
+        """SM cycles of the last chain run by role (zeros unless set_chain_profile was on):
+        committer waiting, validity, decision, applying, loop total; team leaders idle, teams
+        evaluating, evaluations."""
         out = np.zeros(12, np.float64)
         check(self._lib.gcmc_chain_profile(self._h, out.ctypes.data_as(C.c_void_p)), self._h)
         keys = ("commit_wait", "commit_valid", "commit_decide", "commit_apply", "commit_total",

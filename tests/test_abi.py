@@ -71,6 +71,7 @@ def test_null_and_bad_arguments_without_gpu():
     assert L.gcmc_create(C.byref(p), None, C.byref(h)) == 1
     assert L.gcmc_destroy(None) == 0
     assert L.gcmc_last_error(None) == b"null context"
+    assert L.gcmc_set_chain_profile(None, 1) == 1
 
 
 def test_species_major_order():

@@ -195,3 +195,29 @@ def test_batched_prepare_and_gradient_match_per_box_calls(precision):
             a0 = np.sort(st0[3][bounds[c]:bounds[c + 1]])
             a1 = np.sort(st1[3][bounds[c]:bounds[c + 1]])
             assert np.array_equal(a0, a1)
+
+
+def test_cycle_counters_only_when_asked_and_same_moves():
+    """The per-role cycle counters are compiled in only for a profiled run;
+    the profiled kernel takes the same moves and decisions."""
+    L = W.box_edge(900, 0.45)
+    pos = _relaxed(900, L, 7)
+    mix = Mix(1 / 3, 1 / 3, 1 / 3, 0.3, 1 / 1.2, [-2.7])
+    traces, profs = [], []
+    for on in (False, True):
+        b = Box(L, 2.5, [[1.0]], [[1.0]], precision="fp32")
+        b.set_chain_config(0)
+        b.set_chain_profile(on)
+        b.build_cells(torch.as_tensor(pos), torch.zeros(900, dtype=torch.int32))
+        _, tr = b.run_moves(13, 0, 6000, mix, trace=True)
+        traces.append(tr)
+        profs.append(b.chain_profile())
+    off, on = profs
+    assert all(off[k] == 0 for k in off if k != "evaluations")
+    assert off["evaluations"] >= 6000
+    assert on["commit_total"] > 0 and on["team_eval"] > 0
+    assert on["commit_total"] >= on["commit_wait"] + on["commit_valid"] + on["commit_decide"]
+    for k in ("type", "species", "index", "accepted"):
+        assert np.array_equal(traces[0][k], traces[1][k]), k
+    from paper_1408_3764_gb300 import _lib
+    assert _lib.load().gcmc_set_chain_profile(b.handle, 2) == 1  # INVALID_ARG

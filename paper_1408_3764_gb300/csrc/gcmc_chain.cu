@@ -300,10 +300,13 @@ __device__ __forceinline__ void pair_terms(const uint4 &P, const uint4 &q, const
 // The Metropolis test of Eqs. 3-5 (textbook sign of mu) in FP32 with an
 // explicit error band: 1 accept, 0 reject, -1 inside the band or not finite
 // (the caller decides in FP64).  ns: N_s before the move.
-// lnK: ln of the move's count and activity factor (0 for displacements),
-// known before the trial's energy change.
-__device__ __forceinline__ int decide_f32(float beta_f, float tol_f, float lnK, float lnu, float dUf, float uab)
+__device__ __forceinline__ int decide_f32(const ChainArgs &a, int type, int sp, float ln_ns, float ln_ns1, float lnu,
+                                          float dUf, float uab)
 {
+    const float beta_f = a.beta_f, tol_f = a.tol_f;
+    float lnK = 0.f;
+    if (type == 1) lnK = a.lnzv_f[sp] - ln_ns1;
+    else if (type == 2) lnK = ln_ns - a.lnzv_f[sp];
     const float lnA = lnK - beta_f * dUf;
     const float band = beta_f * tol_f * uab + 1e-6f * (1.f + fabsf(lnK) + fabsf(beta_f * dUf) + fabsf(lnu));
     const float diff = lnu - lnA;
@@ -1371,7 +1374,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
         unsigned long long cw = 0, cv = 0, cd = 0, ca = 0, ct = 0;  // committer cycles (see ChainOut::prof)
         unsigned long long cv_e = 0, cv_l = 0, cv_p = 0, cb = 0;
         int nacc = 0;  // moves accepted so far (the committer's count, published in sh.nacc)
-        const float beta_f = a.beta_f, tol_f = a.tol_f;
         for (int m = 0; m < n; ++m) {
             const unsigned long long tm0 = prof_clock<PROF>();
             Slot &S = sh.slots[(m) & (kRS - 1)];
@@ -1397,9 +1399,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             }
             int c0 = 0, attempt = 0;
             Trial tcur;
-            long long ns_m = 0;
-            float lnK_m = 0.f, lnu_m = 0.f;
-            int full_m = 0;
             for (;; ++attempt) {
                 // wait for the trial of m (its evaluation under way) and for
                 // room in the keeper's book
@@ -1429,20 +1428,6 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 __threadfence_block();
                 c0 = S.c0;
                 tcur = S.t;  // one copy in registers for the checks and the decision
-                // the decision's inputs that do not depend on the sums: the
-                // counts at the move's turn are final (every earlier move is
-                // committed), and so are the cell counts
-                {
-                    const int sp = tcur.s;
-                    ns_m = sh.n[sp];
-                    lnK_m = 0.f;
-                    if (tcur.type == 1) lnK_m = a.lnzv_f[sp] - sh.ln_n1[sp];
-                    else if (tcur.type == 2) lnK_m = sh.ln_n[sp] - a.lnzv_f[sp];
-                    lnu_m = C.words(m).lnu;
-                    full_m = 0;
-                    if (tcur.type == 1 && ns_m >= a.maxN) full_m = kStatusCapacity;
-                    else if ((tcur.type == 1 || tcur.cross) && cnt[tcur.cn] >= a.cap) full_m = kStatusCellOverflow;
-                }
                 // While the team evaluates, check what does not depend on its
                 // sums (the moves [c0, m) are all committed by now).  The
                 // counts at the move's turn equal those the evaluation picked
@@ -1525,9 +1510,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
             }
             int refined = attempt > 0 ? 4 : 0;
             const int type = t.type, sp = t.s;
-            const long long ns = ns_m;
+            const long long ns = sh.n[sp];
             // the Metropolis test in FP32 with an error band
-            const int dec = t.possible ? decide_f32(beta_f, tol_f, lnK_m, lnu_m, e.hi + e.lo, uab) : 0;
+            const int dec = t.possible ? decide_f32(a, type, sp, sh.ln_n[sp], sh.ln_n1[sp], C.words(m).lnu, e.hi + e.lo, uab)
+                                       : 0;
             int fin = dec == 1 ? 1 : 0, use64 = F32 ? 0 : 1;
             double lnA_d = 0.0;
             if (dec < 0) {
@@ -1559,7 +1545,11 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1) k_chain(const ChainArgs *
                 const int lk = 2 * acc_id[q] > att_id[q];
                 if (lk != sh.likely[q]) vstore(sh.likely[q], lk);
             }
-            const int stop_bits = (fin & 1) ? full_m : 0;
+            int stop_bits = 0;
+            if (fin & 1) {
+                if (type == 1 && ns >= a.maxN) stop_bits = kStatusCapacity;
+                else if ((type == 1 || t.cross) && cnt[t.cn] >= a.cap) stop_bits = kStatusCellOverflow;
+            }
             if (stop_bits) {
                 if (lane == 0) {
                     atomicOr(&sh.status, stop_bits);

@@ -65,8 +65,37 @@ FLUSH_BYTES = 256 << 20
 # moves) from an ncu capture (profiles/k_chain_isotherm_fp32.md), valid for
 # the chain kernel source with this sha256 prefix only
 CHAIN_TRAFFIC = {"sha256_prefix": "19137a71284994a4", "bytes": 19.05e6, "moves": 6.4e6}
+# DRAM bytes (read + write, summed over the call's launches) of the timed calls
+# of --kernels-only from one ncu capture (profiles/cell_build_mixture_1m.md),
+# valid for the sources whose joint sha256 has this prefix
+KERNEL_TRAFFIC = {
+    "cells": {"sources": ("gcmc_cells.cu", "gcmc_device.cuh"), "sha256_prefix": "820ee9a4c2fb519e",
+              "bytes": {"cell_build_mixture_1m": 115.4e6}},
+    "energy": {"sources": ("gcmc_energy.cu", "gcmc_stage.cuh", "gcmc_device.cuh"),
+               "sha256_prefix": "13f89e1759c1ac26",
+               "bytes": {"trial_energy_mixture_1m": 151.6e6, "total_energy_mixture_1m": 17.97e6,
+                         "energy_grad_262k": 6.39e6}},
+}
 DEFAULT_MOVES = {"isotherm": 100_000, "c2": 1_000_000, "c1": 10_000}
 DEFAULT_CPU_MOVES = {"isotherm": 20_000, "c2": 1_000_000, "c1": 10_000}
+
+
+def _kernel_traffic(name):
+    """The captured DRAM bytes of a --kernels-only call, or None when its
+    sources changed since the capture."""
+    import hashlib
+    for ref in KERNEL_TRAFFIC.values():
+        if name not in ref["bytes"]:
+            continue
+        h = hashlib.sha256()
+        try:
+            for f in ref["sources"]:
+                with open(os.path.join(ROOT, "paper_1408_3764_gb300", "csrc", f), "rb") as fh:
+                    h.update(fh.read())
+        except OSError:
+            return None
+        return ref["bytes"][name] if h.hexdigest().startswith(ref["sha256_prefix"]) else None
+    return None
 
 
 def _args():
@@ -721,6 +750,8 @@ def _kernel_figures(dev, flush, peaks):
     out["energy_grad_262k"] = {"particles": w5.n, "ms": ms_grad, "particles_per_s": w5.n / (ms_grad / 1e3),
                                "unique_pairs_in_rc": w5.n * inr5 / 2,
                                "roofline": alu(w5.n * inr5 / 2, 30, ms_grad)}
+    for name, v in out.items():
+        v["roofline"]["traffic"] = _kernel_traffic(name)
     return out
 
 

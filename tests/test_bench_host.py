@@ -72,3 +72,20 @@ def test_reference_arm_is_silent_on_other_ranks():
                         "--cpu-moves", "200"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_kernel_traffic_follows_the_sources():
+    """The captured DRAM bytes of the --kernels-only calls are reported only
+    while the kernels' sources hash to the captured prefix."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._kernel_traffic("nothing") is None
+    for name in ("cell_build_mixture_1m", "trial_energy_mixture_1m", "total_energy_mixture_1m",
+                 "energy_grad_262k"):
+        assert bench._kernel_traffic(name) > 0, name
+    saved = dict(bench.KERNEL_TRAFFIC["cells"])
+    try:
+        bench.KERNEL_TRAFFIC["cells"]["sha256_prefix"] = "0" * 16
+        assert bench._kernel_traffic("cell_build_mixture_1m") is None
+    finally:
+        bench.KERNEL_TRAFFIC["cells"].update(saved)

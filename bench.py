@@ -63,8 +63,9 @@ UNIT = "moves/s"
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one full-size chain launch (64 chains x 10^5
 # moves) from an ncu capture (profiles/k_chain_isotherm_fp32.md), valid for
-# the chain kernel source with this sha256 prefix only
-CHAIN_TRAFFIC = {"sha256_prefix": "19137a71284994a4", "bytes": 19.05e6, "moves": 6.4e6}
+# the chain kernel source with this sha256 prefix only (captured with the
+# source 19137a71284994a4, which differs from this one in comments only)
+CHAIN_TRAFFIC = {"sha256_prefix": "fb1ab48a525325ae", "bytes": 19.05e6, "moves": 6.4e6}
 # DRAM bytes (read + write, summed over the call's launches) of the timed calls
 # of --kernels-only from one ncu capture (profiles/cell_build_mixture_1m.md),
 # valid for the sources whose joint sha256 has this prefix

@@ -5,11 +5,13 @@
 //
 // One CTA owns one chain.  Its warps have three roles:
 //
-//  * evaluator teams (warps 1..G*NTEAM): team k evaluates moves k, k + NTEAM,
-//    ..., each as soon as fewer than LOOK moves separate it from the
-//    committer.  An evaluation is speculative: it reads the configuration as
-//    it stands when it starts (after `c0` committed moves, with the particle
-//    counts predicted at the move's turn) and produces the trial, its energy
+//  * evaluator teams (NTEAM teams of G warps, placed off the committer's SM
+//    sub-partition first): team k evaluates moves k, k + NTEAM, ..., each as
+//    soon as fewer than LOOK moves separate it from the committer.  An
+//    evaluation is speculative: it reads the configuration as it stands when
+//    it starts (after `c0` committed moves; the particle pick uses the counts
+//    predicted at the move's turn unless it is the same for every count the
+//    pending moves can leave) and produces the trial, its energy
 //    change dU over the 27 neighbour cells (Algorithms 6 and 7; the union of
 //    both neighbourhoods for a displacement into an adjacent cell), the error
 //    scale uabs and the slots the update will need.  The team's warps split
@@ -26,8 +28,11 @@
 //    applies an accepted move (Sec. 3.2.5: swap-with-last removal, append,
 //    species index refill).  Every decision is therefore the one the
 //    sequential chain takes;
-//  * the keeper (last warp) keeps the FP64 running energy, the averages, the
+//  * the keeper (warp 4) keeps the FP64 running energy, the averages, the
 //    counters and the trace, and refills the ring of Philox4x32-10 words.
+//
+// A profiled launch (PROF) also counts SM cycles per role; the clock reads
+// are compiled out of the launches that do not ask for them.
 //
 // Warps hand work to each other through shared-memory rings and counters
 // with block-scope fences; every wait is bounded and sets a timeout status

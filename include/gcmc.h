@@ -355,8 +355,9 @@ gcmc_status gcmc_chain_profile(gcmc_ctx *ctx, double *cycles);
 gcmc_status gcmc_set_chain_profile(gcmc_ctx *ctx, int32_t on);
 
 /* Team shape of the chain kernel (how its warps split the evaluation of
- * upcoming moves; warps per team, teams, moves a team may run ahead of the
- * committer: 0 = (6, 2, 4), 1 = (7, 2, 4), 2 = (4, 3, 6), 3 = (3, 4, 8)):
+ * upcoming moves; warps per team, teams, look-ahead L -- a move is
+ * evaluated once fewer than L moves separate it from the last committed
+ * one: 0 = (6, 2, 4), 1 = (7, 2, 4), 2 = (4, 3, 6), 3 = (3, 4, 8)):
  * 0 .. GCMC_CHAIN_CONFIGS-1, or -1 to time every shape
  * during the next gcmc_run_moves (after a first quarter of its moves under
  * shape 0) and keep the fastest.  Every shape takes the same moves and
